@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark of the X-engine hot path on B300: full-band Pathfinder integration.
+
+Workload (one "step"): the full 400 MHz CHIME Pathfinder band, N = 256 inputs x F = 1024 channels,
+a stream of 64 frames of T = 4096 samples (0.671 s of sky at 390,625 samples/s per channel). Each
+frame arrives as 131,072 UDP packets (16-byte header + 8 KiB payload, 128 streams of 8 channels)
+already resident in HBM; per frame: xe_assemble (packets -> frame, loss zero-fill) then
+xe_correlate with accumulation; at the end of the integration xe_normalize. Inputs are synthetic
+(seeded noise + 3 point sources, 4+4-bit), 64 distinct frames, ~69 GB of packets: larger than L2.
+
+Prints one JSON line (rank 0). Metric: CMAC/s (complex multiply-accumulates of the upper-triangle
+visibilities, F * N(N+1)/2 * T per frame) and the real-time factor.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xe|reference] [--frames 64]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_INPUTS = 256
+N_CHAN = 1024
+N_TIME = 4096
+N_FRAMES = 64
+GROUPS_PER_STREAM = 1          # 128 streams of 8 channels (one 10GbE link each)
+SAMPLE_RATE = 390625.0         # samples/s per channel: 400 MHz / 1024 channels
+METRIC = "X-engine CMAC/s & real-time factor at N=256x1024 ch; int8 pipe %; p99 latency"
+
+
+def npairs(n):
+    return n * (n + 1) // 2
+
+
+def cmac_per_frame(N=N_INPUTS, F=N_CHAN, T=N_TIME):
+    return F * npairs(N) * T
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.out.flush()
+        self.out.seek(0)
+        rows = [r.split(",") for r in self.out.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.out.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        loaded = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) arm
+
+def cpu_oracle_sample(min_seconds: float = 10.0, max_frames: int = N_FRAMES, channels: int = 16, seed: int = 3):
+    """The oracle as it stands on a bounded sample of the workload: `channels` channels (2 streams of
+    8) of consecutive frames through oracle assembly, correlation, counts and normalisation, adding
+    frames until about `min_seconds` of CPU work. Input generation is not timed."""
+    import numpy as np
+
+    import oracle
+    import synth
+
+    N, T = N_INPUTS, N_TIME
+    lost = np.zeros(channels, np.uint32)
+    vis = None
+    dt = 0.0
+    frames = 0
+    for k in range(max_frames):
+        if dt >= min_seconds:
+            break
+        frames += 1
+        fr = synth.signal_frame(N, channels, T, seed + k)
+        pk = synth.packetize(fr, k * T // 4, GROUPS_PER_STREAM)
+        ts = time.perf_counter()
+        frame, _, lost, _ = oracle.assemble(pk, k * T // 4, GROUPS_PER_STREAM, N, channels, T, lost=lost)
+        v, _ = oracle.correlate(frame)
+        vis = v if vis is None else vis + v
+        dt += time.perf_counter() - ts
+    ts = time.perf_counter()
+    n = oracle.counts_from_counters(frames * T, lost, N)
+    oracle.normalize(vis, n)
+    dt += time.perf_counter() - ts
+    cmac = channels * npairs(N) * T * frames
+    return {"value": cmac / dt, "unit": "CMAC/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{channels} channels x {frames} frame(s) of T={T}, N={N}: packets -> assemble -> "
+                      f"correlate -> counts -> normalise ({dt:.1f} s of CPU work)",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    base = None
+    for _ in range(args.steps):
+        base = cpu_oracle_sample()
+        vals.append(base["value"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "CMAC/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": base["seconds"] * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": workload_config(args),
+            "realtime_factor": v / (N_CHAN * npairs(N_INPUTS) * SAMPLE_RATE),
+            "cpu_baseline": {k: base[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": v, "unit": "CMAC/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(args):
+    return {"workload": f"full band batched: N={N_INPUTS}, F={N_CHAN} channels, {args.frames} frames x "
+                        f"T={N_TIME} from 16-byte-header UDP packets (128 streams x 8 ch), assemble + "
+                        f"correlate (accumulate) per frame, normalise per integration",
+            "n_inputs": N_INPUTS, "n_chan": N_CHAN, "n_time": N_TIME, "frames": args.frames,
+            "l2": "inputs larger than L2 (distinct packets per frame)", "parallelism": f"replica x{args.gpus}"}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def make_packets(frames: int, device, seed: int = 3000, p_drop: float = 0.001):
+    """64 distinct frames of synthetic packets, generated on the device (torch RNG), 0.1% dropped."""
+    import torch
+
+    import synth
+
+    pkts, counts = [], []
+    for k in range(frames):
+        fr = synth.signal_frame_torch(N_INPUTS, N_CHAN, N_TIME, seed + k, device=device, chunk=128)
+        pk = synth.packetize_torch(fr, k * N_TIME // 4, GROUPS_PER_STREAM)
+        del fr
+        g = torch.Generator(device=device)
+        g.manual_seed(seed + 7 * k)
+        keep = torch.rand(pk.shape[0], generator=g, device=device) >= p_drop
+        pk = pk[keep].contiguous()
+        pkts.append(pk)
+        counts.append(pk.shape[0])
+    return pkts, counts
+
+
+def run_xe(args):
+    import torch
+
+    import paper_1503_06189_b300 as xe
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    N, F, T, FR = N_INPUTS, N_CHAN, N_TIME, args.frames
+    s = xe.Shape(N, F, T)
+    pkts, counts = make_packets(FR, dev, seed=3000 + 100000 * rank)
+    stride = pkts[0].shape[1]
+    frame = torch.empty((T, F, N), dtype=torch.uint8, device=dev)
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
+    lost = torch.zeros(F, dtype=torch.int32, device=dev)
+    stats = torch.zeros(5, dtype=torch.int32, device=dev)
+    vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
+    out = torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev)
+    ws_a = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
+    ws_c = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    n_ev = FR * max(args.steps, 1)
+    ev_c0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    ev_c1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    launches_per_step = FR * (3 + 2) + 1
+
+    def step(ev_base=None):
+        lost.zero_()
+        for k in range(FR):
+            xe.xe_assemble(pkts[k], counts[k], stride, k * T // 4, GROUPS_PER_STREAM, s, frame, filled, lost,
+                           stats, ws_a, stream=stream)
+            if ev_base is not None:
+                ev_c0[ev_base + k].record(stream)
+            xe.xe_correlate(frame, s, vis, k > 0, ws_c, stream=stream)
+            if ev_base is not None:
+                ev_c1[ev_base + k].record(stream)
+        xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for k in range(args.steps):
+            step(ev_base=k * FR)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    corr_ms = [ev_c0[k].elapsed_time(ev_c1[k]) for k in range(n_ev)]
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = clk.summary()
+    print(f"[bench] device: {ms:.3f} ms/step, correlate {statistics.mean(corr_ms):.4f} ms/launch, clocks {clocks}",
+          file=sys.stderr, flush=True)
+
+    # end to end through host buffers: pinned packets -> H2D per frame -> same calls -> D2H of result
+    e2e = run_e2e(xe, torch, dev, pkts, counts, stride, args)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    cmac_step = cmac_per_frame() * FR
+    value = cmac_step / (ms / 1e3) * world
+    pk, how = peaks()
+    peak_tflops = 2.0 * pk["bf16_tflops_sustained"]      # FP8 dense = 2 x bf16 (nominal ratio)
+    corr_avg_ms = statistics.mean(corr_ms)
+    achieved = cmac_per_frame() * 8 / (corr_avg_ms / 1e3) / 1e12
+    traffic = load_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "CMAC/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e5m2 x e5m2 -> f32 (exact int), int32 out", "data": "synthetic",
+        "config": workload_config(args),
+        "realtime_factor": FR * T / SAMPLE_RATE / (ms / 1e3),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "xe_correlate (unpack + tcgen05 GEMM), 8 int ops per CMAC",
+                     "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if world == 1 or rank == 0:
+        line["cpu_baseline"] = {k: v for k, v in cpu_oracle_sample().items() if k != "seconds"}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def load_traffic():
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(p):
+        return json.load(open(p)).get("correlate_bytes_per_launch")
+    return None
+
+
+def run_e2e(xe, torch, dev, pkts, counts, stride, args):
+    """Same integration through host buffers: each frame's packets are copied from pinned host memory
+    (a ring of 4 distinct frames) on a copy stream, double-buffered against compute; the normalised
+    matrix is copied back at the end of every step."""
+    N, F, T, FR = N_INPUTS, N_CHAN, N_TIME, args.frames
+    s = xe.Shape(N, F, T)
+    ring = [pkts[k].cpu().pin_memory() for k in range(min(4, FR))]
+    rcount = [counts[k] for k in range(len(ring))]
+    dbuf = [torch.empty((max(rcount), stride), dtype=torch.uint8, device=dev) for _ in range(2)]
+    frame = torch.empty((T, F, N), dtype=torch.uint8, device=dev)
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
+    lost = torch.zeros(F, dtype=torch.int32, device=dev)
+    stats = torch.zeros(5, dtype=torch.int32, device=dev)
+    vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
+    out = torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev)
+    host_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
+    ws_a = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
+    ws_c = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
+    comp = torch.cuda.Stream(device=dev)
+    copy = torch.cuda.Stream(device=dev)
+    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    used = [torch.cuda.Event() for _ in range(2)]
+    h2d_bytes = 0
+
+    def one_step():
+        nonlocal h2d_bytes
+        lost.zero_()
+        for k in range(FR):
+            b = k % 2
+            src = ring[k % len(ring)]
+            with torch.cuda.stream(copy):
+                copy.wait_event(used[b])
+                dbuf[b][:src.shape[0]].copy_(src, non_blocking=True)
+                h2d_done[b].record(copy)
+            comp.wait_event(h2d_done[b])
+            xe.xe_assemble(dbuf[b], rcount[k % len(ring)], stride, k * T // 4, GROUPS_PER_STREAM, s, frame,
+                           filled, lost, stats, ws_a, stream=comp)
+            used[b].record(comp)
+            xe.xe_correlate(frame, s, vis, k > 0, ws_c, stream=comp)
+        xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=comp)
+        with torch.cuda.stream(comp):
+            host_out.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        one_step()
+    torch.cuda.synchronize(dev)
+    steps = max(1, args.steps)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one_step()
+        comp.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    h2d = sum(ring[k % len(ring)].numel() for k in range(FR))
+    return {"value": cmac_per_frame() * FR / dt, "unit": "CMAC/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": dt * 1e3,
+            "realtime_factor": FR * T / SAMPLE_RATE / dt}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--frames", type=int, default=N_FRAMES)
+    ap.add_argument("--impl", choices=["xe", "reference"], default="xe")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_xe(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

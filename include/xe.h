@@ -1,0 +1,187 @@
+/*
+ * xe.h -- C ABI of libxe, a B300 (sm_103a) X-engine for 4+4-bit complex radio-correlator data.
+ *
+ * The operations follow Recnik et al., "An Efficient Real-time Data Pipeline for the CHIME
+ * Pathfinder Radio Telescope X-Engine": packet-to-frame assembly (Sec. II-A), cross-correlation
+ * and integration of all input pairs per frequency channel (Sec. I, Sec. II-B), and the
+ * normalisation of the integrated matrix by per-visibility sample counts (Sec. II-C).
+ *
+ * Conventions shared by every call
+ *   - Samples are one byte: high nibble = real, low nibble = imaginary, 4-bit two's complement
+ *     in [-8, 7]. A frame is uint8 [T][F][N] (time, channel, input), N a multiple of 16.
+ *   - Visibilities V_f[i,j] = sum_t x_i(t) conj(x_j(t)) for i <= j are stored as int32 [F][P][2]
+ *     with P = N(N+1)/2, packed row-major upper triangle including the diagonal, {re, im}.
+ *     Position of (i, j): p = i*N - i*(i-1)/2 + (j - i).
+ *   - Every pointer argument is a DEVICE pointer owned by the caller unless stated otherwise; the
+ *     library allocates no device memory on any of these calls. Scratch space ("workspace") is
+ *     sized by the matching *_workspace_size() call and passed in by the caller.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Calls only enqueue work on
+ *     it and return; they never synchronise, except where stated.
+ *   - Every call returns a status: XE_OK or a negative XE_E* code; on error nothing is enqueued.
+ *     Device-side bounded waits that expire record XE_ETIMEOUT in a device status word read by
+ *     xe_device_status().
+ */
+#ifndef XE_H
+#define XE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XE_OK 0
+#define XE_EINVAL (-1)      /* bad shape, pointer, alignment or argument */
+#define XE_EOVERFLOW (-2)   /* T (or an integration length) beyond the int32 bound 2^24 - 1 */
+#define XE_ENOMEM (-3)      /* workspace too small, or over the configured device-memory budget */
+#define XE_ECUDA (-4)       /* a CUDA runtime/driver call failed; see xe_last_cuda_error() */
+#define XE_ETIMEOUT (-5)    /* a bounded device or host wait expired */
+#define XE_EAGAIN (-6)      /* no free slot right now (admission); retry later */
+
+/* Largest time-sample count whose int32 sums cannot overflow: |re V| <= 128 per sample, so
+ * 128 * (2^24 - 1) = 2^31 - 128 is the largest reachable value. */
+#define XE_MAX_TIME 16777215
+
+typedef struct {
+    int32_t n_inputs;   /* N: inputs (antenna feeds x polarisations), multiple of 16 */
+    int32_t n_chan;     /* F: frequency channels */
+    int32_t n_time;     /* T: time samples */
+} xe_shape;
+
+/* ---------------------------------------------------------------- library */
+
+/* Human-readable text of a status code. Never NULL. */
+const char *xe_strerror(int status);
+/* cudaError_t of the last failing CUDA call in this thread (0 if none). */
+int xe_last_cuda_error(void);
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int xe_version(void);
+/* Reads and clears the device status word on the current device (XE_OK or XE_ETIMEOUT).
+ * Synchronises `stream`. */
+int xe_device_status(int *status_out, void *stream);
+/* Failure-detection self test: enqueues one kernel that waits on a flag nothing ever sets, with
+ * a limit of `timeout_ns` nanoseconds, then records XE_ETIMEOUT in the device status word and
+ * returns. The context stays usable. */
+int xe_selftest_timeout(uint64_t timeout_ns, void *stream);
+
+/* ---------------------------------------------------------------- A1: assembly (Sec. II-A) */
+
+/*
+ * Frame assembly from UDP packets (Sec. II-A.2): each packet's data section is placed at the slot
+ * its sequence number gives, lost packets leave zeros, out-of-order packets land by sequence
+ * number, duplicates are ignored. Channel groups of all streams are placed at their global
+ * channel index, which combines the streams of a server (Sec. II, Sec. II-C).
+ *
+ *   pkts        device, n_pkts records of pkt_stride bytes, in arrival order. Record layout:
+ *               16-byte little-endian header {u16 stream_id; u16 chan_group; u32 reserved;
+ *               u64 seq} then the payload [4 t][8 f][N n] bytes. pkt_stride % 16 == 0 and
+ *               pkt_stride >= 16 + 32 N.
+ *   seq0        sequence number of the frame's first slot; the frame covers slots seq0 ..
+ *               seq0 + T/4 - 1 (seq counts packets = 4 time samples).
+ *   groups_per_stream  channel groups (8 channels each) per stream; the global group of a packet
+ *               is stream_id * groups_per_stream + chan_group, channels [8G, 8G + 8).
+ *   s           frame shape; T % 4 == 0, F % 8 == 0, (F/8) % groups_per_stream == 0.
+ *   frame       out, uint8 [T][F][N]; every byte is written (payload or zero).
+ *   filled      out, uint8 [T/4][F/8]; 1 where the slot's packet arrived.
+ *   lost        in/out, uint32 [F]; += 4 for every missing packet of the channel's group
+ *               (lost samples per channel, summed over an integration by the caller).
+ *   stats       in/out, uint32 [5]; += {ok, duplicate, late (seq < seq0), early (seq >= end),
+ *               invalid (stream or group outside the frame)}.
+ *   ws          workspace of xe_assemble_workspace_size(s) bytes (any contents).
+ * The first arrival of a slot wins; results do not depend on thread timing.
+ */
+size_t xe_assemble_workspace_size(xe_shape s);
+int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
+                int32_t groups_per_stream, xe_shape s, uint8_t *frame, uint8_t *filled,
+                uint32_t *lost, uint32_t *stats, void *ws, size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- A2: unpack */
+
+/*
+ * Unpack a frame into the tensor-core operand of the correlation: for channel f, row 2n holds
+ * Re x_n(t) and row 2n+1 holds Im x_n(t), t along the row, each value as an FP8 E5M2 code (the
+ * integers -8..7 are exact in E5M2). Sec. II-B: the packed 4-bit data cross the host link
+ * unpromoted; the promotion happens here on the device.
+ *   y      out, uint8 [F][R][ldy] with R = round_up(2N, 128); rows 2N..R-1 and columns T..ldy-1
+ *          are written as zeros. ldy % 128 == 0 and ldy >= T.
+ */
+int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *stream);
+
+/* ---------------------------------------------------------------- A3/A4: correlation */
+
+/* Engines of the correlation. */
+#define XE_ENGINE_AUTO 0      /* the tuned default */
+#define XE_ENGINE_UNPACKED 1  /* A2 unpack to HBM, then the tcgen05 GEMM reads the E5M2 operand */
+#define XE_ENGINE_FUSED 2     /* the tcgen05 GEMM reads packed bytes and unpacks in shared memory */
+
+typedef struct {
+    int32_t engine;      /* XE_ENGINE_* */
+    int32_t max_strip;   /* 1..4: 128x128 tiles per work item along a row (TMEM columns / 128) */
+    int32_t k_flush;     /* time samples accumulated in TMEM before draining to int32; multiple
+                            of 128; 0 = default */
+    int32_t n_ctas;      /* persistent CTAs; 0 = one per SM */
+} xe_tune;
+
+/*
+ * Cross-correlation of all input pairs for every channel of one frame (Sec. I: the X-engine
+ * correlates all inputs against one another within each band; Sec. II-B: kernels do the
+ * cross-correlation and integration, adding to the previous output).
+ *   frame       device, uint8 [T][F][N]
+ *   vis         in/out, int32 [F][P][2]; written when accumulate == 0, added to otherwise
+ *               (integration over frames, Sec. II-B). The caller keeps the integrated sample
+ *               count <= XE_MAX_TIME.
+ *   ws          workspace of xe_correlate_workspace_size(s) bytes.
+ * Results are bit-exact integers. Errors: XE_EINVAL (shape: N % 16, N < 16, F < 1, T < 0, or
+ * N > 4096), XE_EOVERFLOW (T > XE_MAX_TIME), XE_ENOMEM (ws too small).
+ */
+size_t xe_correlate_workspace_size(xe_shape s);
+int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate, void *ws,
+                 size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- A6: batched persistent */
+
+#define XE_MAX_JOBS 64
+
+typedef struct {
+    const uint8_t *frame;  /* device, uint8 [T][F][N] */
+    int32_t *vis;          /* device, int32 [F][P][2] */
+    xe_shape s;
+    int32_t accumulate;    /* 0: write, 1: add */
+} xe_job;
+
+/*
+ * All channels of up to XE_MAX_JOBS frames, of possibly different N, F and T, in one persistent
+ * launch (Sec. II-B: chains of operations are preloaded to hide launch latency). `jobs` is a HOST
+ * array, read during the call. `tune` may be NULL (tuned defaults). The launch is capturable in a
+ * CUDA graph. Same per-job rules and errors as xe_correlate.
+ */
+size_t xe_correlate_batched_workspace_size(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune);
+int xe_correlate_batched(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune, void *ws,
+                         size_t ws_bytes, void *stream);
+
+/* ---------------------------------------------------------------- A5: normalisation (Sec. II-C) */
+
+/*
+ * Normalisation by the per-visibility sample count (Sec. II-C): packet loss is one counter per
+ * channel applied to every point of the matrix; F-engine flags are counted per input and channel;
+ * inputs flagged in the same sample are counted back once per pair.
+ *   n_ij = t_int - lost[f] - c[f][i] - c[f][j] + x[f][p(i,j)]   (i != j)
+ *   n_ii = t_int - lost[f] - c[f][i]
+ *   out  = (float)V / (float)n_ij with IEEE division, 0 where n_ij <= 0.
+ *   vis         device, int32 [F][P][2] (integrated visibilities)
+ *   lost        device, uint32 [F]: lost samples per channel over the integration
+ *   flag_count  device, uint32 [F][N] or NULL; flag_pairs device, uint32 [F][P] or NULL (both
+ *               or neither)
+ *   out         out, float [F][P][2];  n_out  out, uint32 [F][P] or NULL
+ * Errors: XE_EINVAL, XE_EOVERFLOW (t_int > XE_MAX_TIME).
+ */
+int xe_normalize(const int32_t *vis, xe_shape s, uint32_t t_int, const uint32_t *lost,
+                 const uint32_t *flag_count, const uint32_t *flag_pairs, float *out,
+                 uint32_t *n_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XE_H */

@@ -1,0 +1,208 @@
+"""Python binding of libxe, the sm_103a X-engine library declared in include/xe.h.
+
+Argument marshalling only: every step of the hot path runs in libxe's CUDA kernels. torch is used
+for device memory and streams. The functions keep the C names; tensors are passed as torch CUDA
+tensors (or raw integer device pointers where noted) and shapes as ``Shape(N, F, T)``.
+
+There is no fallback: if libxe.so is missing or fails to load, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libxe.so")
+
+XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ENOMEM, XE_ECUDA, XE_ETIMEOUT, XE_EAGAIN = 0, -1, -2, -3, -4, -5, -6
+XE_MAX_TIME = (1 << 24) - 1
+XE_MAX_JOBS = 64
+XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED = 0, 1, 2
+
+EXPORTED = [
+    "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",
+    "xe_assemble_workspace_size", "xe_assemble", "xe_unpack", "xe_correlate_workspace_size",
+    "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched", "xe_normalize",
+]
+
+
+class XeError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = _lib.xe_strerror(status).decode() if _lib is not None else str(status)
+        if status == XE_ECUDA and _lib is not None:
+            msg += f" (cudaError {_lib.xe_last_cuda_error()})"
+        super().__init__(f"{what}: {msg} [{status}]")
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int32), ("n_chan", ctypes.c_int32), ("n_time", ctypes.c_int32)]
+
+    def __init__(self, n_inputs=0, n_chan=0, n_time=0):
+        super().__init__(int(n_inputs), int(n_chan), int(n_time))
+
+    def __repr__(self):
+        return f"Shape(N={self.n_inputs}, F={self.n_chan}, T={self.n_time})"
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_void_p), ("vis", ctypes.c_void_p), ("s", Shape), ("accumulate", ctypes.c_int32)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_int32), ("max_strip", ctypes.c_int32), ("k_flush", ctypes.c_int32),
+                ("n_ctas", ctypes.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libxe.so not built at {LIB_PATH}; run `python -m paper_1503_06189_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, sz, i32, u32, u64, i64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
+    L.xe_strerror.restype = ctypes.c_char_p
+    L.xe_strerror.argtypes = [ctypes.c_int]
+    L.xe_last_cuda_error.restype = ctypes.c_int
+    L.xe_version.restype = ctypes.c_int
+    L.xe_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), vp]
+    L.xe_selftest_timeout.argtypes = [u64, vp]
+    L.xe_assemble_workspace_size.restype = sz
+    L.xe_assemble_workspace_size.argtypes = [Shape]
+    L.xe_assemble.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, vp, vp, vp, sz, vp]
+    L.xe_unpack.argtypes = [vp, Shape, vp, i64, vp]
+    L.xe_correlate_workspace_size.restype = sz
+    L.xe_correlate_workspace_size.argtypes = [Shape]
+    L.xe_correlate.argtypes = [vp, Shape, vp, ctypes.c_int, vp, sz, vp]
+    L.xe_correlate_batched_workspace_size.restype = sz
+    L.xe_correlate_batched_workspace_size.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune)]
+    L.xe_correlate_batched.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune), vp, sz, vp]
+    L.xe_normalize.argtypes = [vp, Shape, u32, vp, vp, vp, vp, vp, vp]
+    for name in EXPORTED:
+        getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+# ----------------------------------------------------------------------------- marshalling helpers
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(st: int, what: str):
+    if st != XE_OK:
+        raise XeError(st, what)
+
+
+def _nbytes(t):
+    return 0 if t is None else (t if isinstance(t, int) else t.numel() * t.element_size())
+
+
+def npairs(n: int) -> int:
+    return n * (n + 1) // 2
+
+
+# ----------------------------------------------------------------------------- library
+
+def xe_strerror(status: int) -> str:
+    return _lib.xe_strerror(status).decode()
+
+
+def xe_last_cuda_error() -> int:
+    return _lib.xe_last_cuda_error()
+
+
+def xe_version() -> int:
+    return _lib.xe_version()
+
+
+def xe_device_status(stream=None) -> int:
+    v = ctypes.c_int(0)
+    _check(_lib.xe_device_status(ctypes.byref(v), _stream(stream)), "xe_device_status")
+    return v.value
+
+
+def xe_selftest_timeout(timeout_ns: int, stream=None):
+    _check(_lib.xe_selftest_timeout(timeout_ns, _stream(stream)), "xe_selftest_timeout")
+
+
+# ----------------------------------------------------------------------------- A1
+
+def xe_assemble_workspace_size(shape: Shape) -> int:
+    return _lib.xe_assemble_workspace_size(shape)
+
+
+def xe_assemble(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
+                frame, filled, lost, stats, ws, stream=None):
+    _check(_lib.xe_assemble(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(frame),
+                            _ptr(filled), _ptr(lost), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)),
+           "xe_assemble")
+
+
+# ----------------------------------------------------------------------------- A2..A4
+
+def xe_unpack(frame, shape: Shape, y, ldy: int, stream=None):
+    _check(_lib.xe_unpack(_ptr(frame), shape, _ptr(y), ldy, _stream(stream)), "xe_unpack")
+
+
+def xe_correlate_workspace_size(shape: Shape) -> int:
+    return _lib.xe_correlate_workspace_size(shape)
+
+
+def xe_correlate(frame, shape: Shape, vis, accumulate: bool, ws, stream=None):
+    _check(_lib.xe_correlate(_ptr(frame), shape, _ptr(vis), 1 if accumulate else 0, _ptr(ws), _nbytes(ws),
+                             _stream(stream)), "xe_correlate")
+
+
+def _jobs(jobs):
+    arr = (Job * len(jobs))()
+    for k, (frame, vis, shape, acc) in enumerate(jobs):
+        arr[k] = Job(_ptr(frame), _ptr(vis), shape, 1 if acc else 0)
+    return arr
+
+
+def _tune(tune):
+    if tune is None:
+        return None
+    if isinstance(tune, Tune):
+        return ctypes.byref(tune)
+    return ctypes.byref(Tune(**tune))
+
+
+def xe_correlate_batched_workspace_size(jobs, tune=None) -> int:
+    arr = _jobs(jobs)
+    return _lib.xe_correlate_batched_workspace_size(arr, len(jobs), _tune(tune))
+
+
+def xe_correlate_batched(jobs, ws, tune=None, stream=None):
+    """jobs: sequence of (frame, vis, Shape, accumulate)."""
+    arr = _jobs(jobs)
+    _check(_lib.xe_correlate_batched(arr, len(jobs), _tune(tune), _ptr(ws), _nbytes(ws), _stream(stream)),
+           "xe_correlate_batched")
+
+
+# ----------------------------------------------------------------------------- A5
+
+def xe_normalize(vis, shape: Shape, t_int: int, lost, out, n_out=None, flag_count=None, flag_pairs=None,
+                 stream=None):
+    _check(_lib.xe_normalize(_ptr(vis), shape, t_int, _ptr(lost), _ptr(flag_count), _ptr(flag_pairs), _ptr(out),
+                             _ptr(n_out), _stream(stream)), "xe_normalize")

@@ -1,0 +1,151 @@
+// xe_assemble.cu -- A1: UDP packets -> frame (Sec. II-A).
+//
+// Sec. II-A.2: sequence numbers place each packet's data section in the frame; lost packets leave
+// zeros in their place; out-of-order packets land by sequence number; duplicates are ignored.
+// Sec. II-A.3: the data section is moved with non-temporal (streaming) loads and stores.
+//
+// Three launches, all HBM-bound and independent of thread timing:
+//   1. init   owner[slot][group] = none
+//   2. claim  every in-window packet k does owner = min(owner, k): the first arrival wins
+//   3. copy   packet k copies its payload iff owner == k (else it is a duplicate); every slot that
+//             no packet owns is zero-filled and its 8 channels' lost counters grow by 4 samples.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "xe_internal.h"
+
+namespace xe {
+namespace asmb {
+
+constexpr uint32_t kNone = 0xFFFFFFFFu;
+
+struct Geo {
+    uint64_t seq0;
+    uint32_t n_pkts, stride;
+    int32_t N, F, Q, G, gps, S;
+};
+
+enum Class { kOk = 0, kLate = 2, kEarly = 3, kInvalid = 4 };
+
+__device__ __forceinline__ int classify(const uint8_t *pkts, const Geo &g, uint32_t k, int &slot, int &grp) {
+    const uint4 h = __ldg(reinterpret_cast<const uint4 *>(pkts + (size_t)k * g.stride));
+    const uint32_t sid = h.x & 0xFFFFu, cg = h.x >> 16;
+    const uint64_t seq = (static_cast<uint64_t>(h.w) << 32) | h.z;
+    if (sid >= (uint32_t)g.S || cg >= (uint32_t)g.gps) return kInvalid;
+    if (seq < g.seq0) return kLate;
+    if (seq - g.seq0 >= (uint64_t)g.Q) return kEarly;
+    slot = (int)(seq - g.seq0);
+    grp = (int)(sid * g.gps + cg);
+    return kOk;
+}
+
+__global__ void init_kernel(uint32_t *owner, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        owner[i] = kNone;
+}
+
+__global__ void claim_kernel(const uint8_t *__restrict__ pkts, Geo g, uint32_t *owner, uint32_t *stats) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    int cls = -1, slot = 0, grp = 0;
+    if (k < g.n_pkts) {
+        cls = classify(pkts, g, k, slot, grp);
+        if (cls == kOk) atomicMin(&owner[(size_t)slot * g.G + grp], k);
+    }
+    const uint32_t late = __reduce_add_sync(0xffffffffu, cls == kLate);
+    const uint32_t early = __reduce_add_sync(0xffffffffu, cls == kEarly);
+    const uint32_t inval = __reduce_add_sync(0xffffffffu, cls == kInvalid);
+    if ((threadIdx.x & 31) == 0) {
+        if (late) atomicAdd(&stats[2], late);
+        if (early) atomicAdd(&stats[3], early);
+        if (inval) atomicAdd(&stats[4], inval);
+    }
+}
+
+// One warp per packet (warps [0, n_pkts)) and one warp per (slot, group) (the warps after them).
+__global__ void __launch_bounds__(256) copy_kernel(const uint8_t *__restrict__ pkts, Geo g,
+                                                   const uint32_t *__restrict__ owner, uint8_t *__restrict__ frame,
+                                                   uint8_t *__restrict__ filled, uint32_t *lost, uint32_t *stats) {
+    const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int row_vec = g.N / 2;                  // 16-byte vectors in one 8-channel row (8N bytes)
+    if (wid < g.n_pkts) {
+        const uint32_t k = (uint32_t)wid;
+        int slot = 0, grp = 0;
+        if (classify(pkts, g, k, slot, grp) != kOk) return;
+        const bool mine = owner[(size_t)slot * g.G + grp] == k;
+        if (lane == 0) atomicAdd(&stats[mine ? 0 : 1], 1u);
+        if (!mine) return;
+        const uint4 *src = reinterpret_cast<const uint4 *>(pkts + (size_t)k * g.stride + 16);
+        for (int tt = 0; tt < 4; ++tt) {
+            uint4 *dst = reinterpret_cast<uint4 *>(frame + ((size_t)(4 * slot + tt) * g.F + 8 * grp) * g.N);
+            for (int v = lane; v < row_vec; v += 32) __stcs(dst + v, __ldcs(src + tt * row_vec + v));
+        }
+        return;
+    }
+    const uint64_t sg = wid - g.n_pkts;
+    if (sg >= (uint64_t)g.Q * g.G) return;
+    const int slot = (int)(sg / g.G), grp = (int)(sg % g.G);
+    const bool have = owner[sg] != kNone;
+    if (lane == 0) filled[sg] = have ? 1 : 0;
+    if (have) return;
+    if (lane < 8) atomicAdd(&lost[8 * grp + lane], 4u);
+    const uint4 z = make_uint4(0, 0, 0, 0);
+    for (int tt = 0; tt < 4; ++tt) {
+        uint4 *dst = reinterpret_cast<uint4 *>(frame + ((size_t)(4 * slot + tt) * g.F + 8 * grp) * g.N);
+        for (int v = lane; v < row_vec; v += 32) __stcs(dst + v, z);
+    }
+}
+
+}  // namespace asmb
+}  // namespace xe
+
+using namespace xe;
+
+extern "C" {
+
+size_t xe_assemble_workspace_size(xe_shape s) {
+    if (!valid_shape(s) || s.n_time % 4 || s.n_chan % 8) return 0;
+    return (size_t)round_up((int64_t)(s.n_time / 4) * (s.n_chan / 8) * 4, 256);
+}
+
+int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost, uint32_t *stats, void *ws,
+                size_t ws_bytes, void *stream) {
+    if (!valid_shape(s) || s.n_time < 4 || s.n_time % 4 || s.n_chan % 8 || gps < 1 || (s.n_chan / 8) % gps)
+        return XE_EINVAL;
+    if (!frame || !filled || !lost || !stats || (n_pkts && !pkts)) return XE_EINVAL;
+    if (pkt_stride % 16 || pkt_stride < 16u + 32u * (uint32_t)s.n_inputs) return XE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(pkts) | reinterpret_cast<uintptr_t>(frame)) & 15) return XE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(lost) | reinterpret_cast<uintptr_t>(stats) | reinterpret_cast<uintptr_t>(ws)) & 3)
+        return XE_EINVAL;
+    if (!ws || ws_bytes < xe_assemble_workspace_size(s)) return XE_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    asmb::Geo g;
+    g.seq0 = seq0;
+    g.n_pkts = n_pkts;
+    g.stride = pkt_stride;
+    g.N = s.n_inputs;
+    g.F = s.n_chan;
+    g.Q = s.n_time / 4;
+    g.G = s.n_chan / 8;
+    g.gps = gps;
+    g.S = g.G / gps;
+    uint32_t *owner = static_cast<uint32_t *>(ws);
+    const int64_t slots = (int64_t)g.Q * g.G;
+    asmb::init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
+    XE_TRY_CUDA(cudaGetLastError());
+    if (n_pkts) {
+        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats);
+        XE_TRY_CUDA(cudaGetLastError());
+    }
+    const uint64_t warps = (uint64_t)n_pkts + (uint64_t)slots;
+    const uint64_t blocks = (warps + 7) / 8;
+    if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
+    asmb::copy_kernel<<<(unsigned)blocks, 256, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
+    XE_TRY_CUDA(cudaGetLastError());
+    return XE_OK;
+}
+
+}  // extern "C"

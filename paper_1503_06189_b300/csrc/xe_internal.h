@@ -1,0 +1,50 @@
+// xe_internal.h -- host-side helpers shared by the libxe translation units.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "xe.h"
+
+namespace xe {
+
+// Records a failing CUDA runtime status for xe_last_cuda_error() and maps it to XE_ECUDA.
+int cuda_fail(cudaError_t e);
+
+#define XE_TRY_CUDA(call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return ::xe::cuda_fail(e_);  \
+    } while (0)
+
+// Device address of the library's status word on the current device (nullptr on failure).
+int *status_word();
+
+// Wall-clock limit of every bounded device-side wait, in nanoseconds.
+uint64_t wait_limit_ns();
+
+// SM count of the current device (cached per device).
+int sm_count();
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda needed).
+int encode_tiled(CUtensorMap *map, CUtensorMapDataType dtype, uint32_t rank, void *base,
+                 const uint64_t *dims, const uint64_t *strides_bytes, const uint32_t *box,
+                 CUtensorMapSwizzle swizzle);
+
+#ifdef __CUDACC__
+#define XE_HD __host__ __device__
+#else
+#define XE_HD
+#endif
+
+XE_HD inline int64_t npairs(int64_t n) { return n * (n + 1) / 2; }
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+inline bool valid_shape(const xe_shape &s) {
+    return s.n_inputs >= 16 && s.n_inputs <= 4096 && s.n_inputs % 16 == 0 && s.n_chan >= 1 &&
+           s.n_time >= 0;
+}
+
+}  // namespace xe

@@ -1,0 +1,40 @@
+"""The C-ABI library loads and exports every entry point include/xe.h declares (no GPU, no compute)."""
+import ctypes
+import os
+import re
+
+import paper_1503_06189_b300 as xe
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "xe.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(xe_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_functions():
+    names = declared_functions()
+    assert "xe_correlate" in names and "xe_assemble" in names and "xe_normalize" in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(xe.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    assert sorted(xe.EXPORTED) == declared_functions()
+    for n in declared_functions():
+        assert callable(getattr(xe, n))
+
+
+def test_host_only_calls():
+    assert xe.xe_version() >= 10000
+    assert "overflow" in xe.xe_strerror(xe.XE_EOVERFLOW) or "int32" in xe.xe_strerror(xe.XE_EOVERFLOW)
+    assert xe.xe_correlate_workspace_size(xe.Shape(20, 1, 128)) == 0          # N % 16 != 0
+    s = xe.Shape(256, 64, 16384)
+    assert xe.xe_correlate_workspace_size(s) >= 64 * 512 * 16384
+    assert xe.xe_assemble_workspace_size(xe.Shape(256, 1024, 4096)) == 1024 * 128 * 4

@@ -1,0 +1,49 @@
+"""Helpers that run the CUDA path (through the C-ABI binding) on host numpy inputs (GPU tests)."""
+import numpy as np
+import torch
+
+import paper_1503_06189_b300 as xe
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def correlate(frame, vis=None, accumulate=False):
+    """frame: numpy [T][F][N] u8 or CUDA tensor -> int32 CUDA tensor [F][P][2]."""
+    fr = frame if isinstance(frame, torch.Tensor) else dev(frame)
+    T, F, N = fr.shape
+    s = xe.Shape(N, F, T)
+    if vis is None:
+        vis = torch.full((F, xe.npairs(N), 2), -12345, dtype=torch.int32, device=fr.device)
+    ws = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=fr.device)
+    xe.xe_correlate(fr, s, vis, accumulate, ws)
+    return vis
+
+
+def correlate_batched(frames, tune=None, accumulate=False):
+    jobs, keep = [], []
+    for fr in frames:
+        f = fr if isinstance(fr, torch.Tensor) else dev(fr)
+        T, F, N = f.shape
+        v = torch.full((F, xe.npairs(N), 2), -777, dtype=torch.int32, device=f.device)
+        jobs.append((f, v, xe.Shape(N, F, T), accumulate))
+        keep.append((f, v))
+    ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device="cuda")
+    xe.xe_correlate_batched(jobs, ws, tune)
+    return [v for _, v in keep]
+
+
+def e5m2_codes(frame):
+    """Expected unpack output [F][R][ldy] of a frame, from numpy's float16 (E5M2 = high byte)."""
+    T, F, N = frame.shape
+    b = frame.astype(np.int64)
+    re = ((b >> 4) ^ 8) - 8
+    im = ((b & 15) ^ 8) - 8
+    R = -(-2 * N // 128) * 128
+    ldy = -(-max(T, 1) // 128) * 128
+    out = np.zeros((F, R, ldy), np.uint8)
+    code = lambda v: (v.astype(np.float16).view(np.uint16) >> 8).astype(np.uint8)
+    out[:, 0:2 * N:2, :T] = code(re).transpose(1, 2, 0)
+    out[:, 1:2 * N:2, :T] = code(im).transpose(1, 2, 0)
+    return out, R, ldy
