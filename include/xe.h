@@ -99,25 +99,28 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
 /* ---------------------------------------------------------------- A2: unpack */
 
 /*
- * Unpack a frame into the tensor-core operand of the correlation: for channel f, row 2n holds
- * Re x_n(t) and row 2n+1 holds Im x_n(t), t along the row, each value as an FP8 E5M2 code (the
- * integers -8..7 are exact in E5M2). Sec. II-B: the packed 4-bit data cross the host link
- * unpromoted; the promotion happens here on the device.
- *   y      out, uint8 [F][R][ldy] with R = round_up(2N, 128); rows 2N..R-1 and columns T..ldy-1
- *          are written as zeros. ldy % 128 == 0 and ldy >= T.
+ * Unpack a frame into the tensor-core operand of the correlation (Sec. II-B: the packed 4-bit
+ * data cross the host link unpromoted; the promotion happens here, on the device). For channel f
+ * and sample t, row t of y holds 2N FP8 E5M2 codes in input order, (16 Re x_n(t), Im x_n(t)) for
+ * n = 0..N-1 (the integers are exact in E5M2; the factor 16 is a power of two removed again when
+ * the correlation is drained), then zeros up to R.
+ *   y      out, uint8 [F][ldy][R] with R = round_up(2N, 128); rows T..ldy-1 are zero.
+ *          ldy % 128 == 0 and ldy >= T.
  */
 int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *stream);
 
 /* ---------------------------------------------------------------- A3/A4: correlation */
 
 /* Engines of the correlation. */
-#define XE_ENGINE_AUTO 0      /* the tuned default */
-#define XE_ENGINE_UNPACKED 1  /* A2 unpack to HBM, then the tcgen05 GEMM reads the E5M2 operand */
-#define XE_ENGINE_FUSED 2     /* the tcgen05 GEMM reads packed bytes and unpacks in shared memory */
+#define XE_ENGINE_AUTO 0        /* the tuned default (XE_ENGINE_FUSED) */
+#define XE_ENGINE_UNPACKED 1    /* A2 unpack to HBM (MN-major), then the tcgen05 GEMM reads it */
+#define XE_ENGINE_FUSED 2       /* the GEMM loads packed bytes and expands them in shared memory */
+#define XE_ENGINE_UNPACKED_K 3  /* A2 unpack to HBM transposed (K-major), then the GEMM */
 
 typedef struct {
     int32_t engine;      /* XE_ENGINE_* */
-    int32_t max_strip;   /* 1..4: 128x128 tiles per work item along a row (TMEM columns / 128) */
+    int32_t max_strip;   /* 1..4: 128x128 tiles per work item along a row; <= 2 double-buffers
+                            the tensor-memory accumulator (default 2) */
     int32_t k_flush;     /* time samples accumulated in TMEM before draining to int32; multiple
                             of 128; 0 = default */
     int32_t n_ctas;      /* persistent CTAs; 0 = one per SM */

@@ -4,16 +4,23 @@
 // With x = a + ib and the real matrix Y_f whose row 2n is a_n(t) and row 2n+1 is b_n(t), the Gram
 // matrix G = Y Y^T holds every real product sum, and
 //     Re V[i,j] = G[2i,2j] + G[2i+1,2j+1],     Im V[i,j] = G[2i+1,2j] - G[2i,2j+1].
-// G is computed on the tensor cores with tcgen05.mma kind::f8f6f4: the 4-bit integers -8..7 are
-// exact as FP8 E5M2, their products (|p| <= 64) and every partial sum below 2^24 are exact in the
-// FP32 accumulator held in tensor memory, and the accumulator is drained to int32 at least every
-// k_flush samples. Only 128x128 tiles of G on or above the block diagonal are computed.
+// G is computed on the tensor cores with tcgen05.mma kind::f8f6f4: the 4-bit integers are exact as
+// FP8 E5M2 (the MN-major engines carry 16*a instead of a, also exact), their products and every
+// partial sum below 2^24 (in units of the operand scales) are exact in the FP32 accumulator held in
+// tensor memory, and the accumulator is drained to int32 at least every k_flush samples. Only
+// 128x128 tiles of G on or above the block diagonal are computed.
 //
-// Kernel roles (one persistent CTA per SM, 6 warps):
-//   warp 0      TMA producer: 128x128-byte tiles of Y (one per 128-row block) into a 3-stage ring
-//   warp 1      TMEM owner and MMA issuer (one thread): 4 MMAs of K=32 per block pair per stage
-//   warps 2..5  epilogue: tcgen05.ld of the FP32 tile, FP32 -> int32, 2x2 Re/Im combine across
-//               lane pairs with shfl.xor, store / accumulate into the packed triangle
+// Engines (one kernel template, one persistent CTA per SM):
+//   UNPACKED_K  A2 unpack writes Y K-major [F][R][ldy]; TMA loads 128x128-byte swizzled tiles.
+//   UNPACKED    A2 unpack writes Y MN-major [F][ldy][R] (an in-order byte expansion of the frame);
+//               TMA loads 128 (t) x 128-byte tiles; MMAs read MN-major operands.
+//   FUSED       no unpack: TMA loads packed [128 t][64 n] byte tiles of the frame and converter
+//               warps expand them in shared memory into the MN-major operand layout.
+// Roles: warp 0 = scheduler + TMA producer, warp 1 = TMEM owner + MMA issuer (one thread),
+// warps 2..5 = epilogue (tcgen05.ld, FP32 -> int32, 2x2 Re/Im combine by shfl.xor, store or
+// accumulate into the packed triangle), warps 6..13 = converters (FUSED only).
+// Work items (job, channel, strip) are handed out dynamically (one atomic per item), channel by
+// channel, so that the strips of a channel run together and share its data in L2.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -22,7 +29,6 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
-#include <vector>
 
 #include "xe_device.cuh"
 #include "xe_internal.h"
@@ -30,39 +36,42 @@
 namespace xe {
 namespace corr {
 
-constexpr int kBlk = 128;                         // rows per operand block = MMA M = N
-constexpr int kKt = 128;                          // time samples per pipeline stage (128 B row)
-constexpr int kTileBytes = kBlk * kKt;            // 16 KiB per operand block per stage
-constexpr int kMaxBlocksPerStage = 4;
-constexpr int kStageBytes = kTileBytes * kMaxBlocksPerStage;
-constexpr int kStages = 3;
-constexpr int kThreads = 192;
+constexpr int kBlk = 128;                    // rows per operand block = MMA M
+constexpr int kKt = 128;                     // time samples per pipeline stage
+constexpr int kOpSlotBytes = kBlk * kKt;     // 16 KiB: one operand block for one stage
+constexpr int kPkSlotBytes = 64 * kKt;       // 8 KiB: 64 inputs x 128 samples, packed
 constexpr int kTmemCols = 512;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int kDefaultKFlush = 1 << 17;           // samples; 64 * 2^17 = 2^23 < 2^24
+constexpr int kItemRing = 4;
+constexpr int kSmemMax = 232448;             // 227 KiB opt-in limit per block
+constexpr int kDefaultKFlush = 1 << 17;      // samples; 64 * 2^17 = 2^23 < 2^24
+constexpr int kConvWarps = 8;
 
-struct Job {   // 128-byte aligned through its CUtensorMap
-    CUtensorMap tmap;        // Y operand [F][R][ldy] bytes, box 128 x 128 x 1, 128-byte swizzle
+enum Engine { kUnpackedK = 0, kUnpackedMN = 1, kFusedMN = 2 };
+
+struct Job {                 // 128-byte aligned through its CUtensorMap
+    CUtensorMap tmap;        // operand map (unpacked engines) or packed frame map (fused)
     int32_t *vis;
     int32_t n_inputs, n_chan, n_time, accumulate;
     int32_t nb;              // 128-row operand blocks (R / 128)
     int32_t strips;          // work items per channel
     int32_t k_tiles;         // ceil(T / 128)
     int32_t item_begin;      // first global work-item index of this job
+    int32_t pw;              // fused: bytes per packed row in shared memory (min(64, N))
 };
 
 struct Params {
     Job jobs[XE_MAX_JOBS];
     int32_t n_jobs, n_items, max_strip, k_flush_tiles;
+    int32_t op_stages, pk_stages, slots, n_acc;
     int *status;
+    int *counter;            // work-item counter, zero at launch
     uint64_t limit_ns;
 };
 
 // ----------------------------------------------------------------------------- work items
-// A work item is (job, channel, strip); a strip is a run of up to max_strip tiles along one
-// block row rb, starting at column block cb0 >= rb. The diagonal strip of row rb starts at
-// cb0 = rb (its A operand is its own first B block); further strips hold at most 3 tiles so that
-// A plus the B blocks fit the 4 operand slots of a stage.
+// A strip is a run of up to max_strip tiles along one block row rb, starting at column block
+// cb0 >= rb. The diagonal strip of row rb starts at cb0 = rb (its A operand is its own first B
+// block); further strips hold at most min(max_strip, 3) tiles so A plus the B blocks fit 4 slots.
 
 __host__ __device__ inline int strips_in_row(int nb, int rb, int ms) {
     const int wd = min(ms, nb - rb);
@@ -99,8 +108,11 @@ __host__ __device__ inline void decode_strip(int s, int nb, int ms, int &rb, int
 
 struct Item {
     int job, f, rb, cb0, w;
+    int nblk, a_slot;
+    int blk[4];
 };
 
+// Channel-major order: all strips of one channel are consecutive item indices.
 __device__ __forceinline__ Item decode_item(const Params &p, int g) {
     Item it;
     int j = 0;
@@ -108,19 +120,28 @@ __device__ __forceinline__ Item decode_item(const Params &p, int g) {
     const Job &jb = p.jobs[j];
     const int l = g - jb.item_begin;
     it.job = j;
-    it.f = l % jb.n_chan;
-    decode_strip(l / jb.n_chan, jb.nb, p.max_strip, it.rb, it.cb0, it.w);
+    it.f = l / jb.strips;
+    decode_strip(l % jb.strips, jb.nb, p.max_strip, it.rb, it.cb0, it.w);
+    it.nblk = it.w;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) it.blk[c] = it.cb0 + c;
+    if (it.rb < it.cb0) {
+        it.blk[min(it.nblk, 3)] = it.rb;
+        it.a_slot = it.nblk;
+        ++it.nblk;
+    } else {
+        it.a_slot = 0;
+    }
     return it;
 }
 
-// ----------------------------------------------------------------------------- A2 unpack
+// ----------------------------------------------------------------------------- A2 unpack kernels
 
-// grid (ldy/128, R/128, F), 256 threads: a 128-sample x 64-input byte tile of the frame is staged
-// in shared memory, then written as 128 rows (2n = Re, 2n+1 = Im) of 128 E5M2 codes.
-__global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__ frame,
-                                                     uint8_t *__restrict__ y, int N, int F, int T,
-                                                     int R, int64_t ldy) {
-    __shared__ uint32_t tile[128][17];        // [t][n/4] packed bytes, padded row
+// K-major: grid (ldy/128, R/128, F), 256 threads; a 128-sample x 64-input byte tile is staged in
+// shared memory and written as 128 rows (2n = Re, 2n+1 = Im) of 128 E5M2 codes (unscaled).
+__global__ void __launch_bounds__(256) unpack_k_kernel(const uint8_t *__restrict__ frame, uint8_t *__restrict__ y,
+                                                       int N, int F, int T, int R, int64_t ldy) {
+    __shared__ uint32_t tile[128][17];
     const int t0 = blockIdx.x * 128;
     const int n0 = blockIdx.y * 64;
     const int f = blockIdx.z;
@@ -136,7 +157,7 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
     }
     __syncthreads();
     for (int k = threadIdx.x; k < 1024; k += 256) {
-        const int row = k >> 3, c = k & 7;    // out row 2*nl + comp, 16-sample chunk c
+        const int row = k >> 3, c = k & 7;
         const int nl = row >> 1, comp = row & 1;
         const int shift = (nl & 3) * 8 + (comp ? 0 : 4);
         uint32_t w[4];
@@ -152,19 +173,49 @@ __global__ void __launch_bounds__(256) unpack_kernel(const uint8_t *__restrict__
     }
 }
 
+// MN-major: Y[f][t][0..R) = codes (16 Re x_0, Im x_0, 16 Re x_1, ...), zero past 2N and past T.
+// One thread per 32 output bytes (16 samples in): grid-stride over F * ldy * (R / 32).
+__global__ void __launch_bounds__(256) unpack_mn_kernel(const uint8_t *__restrict__ frame, uint8_t *__restrict__ y,
+                                                        int N, int F, int T, int R, int64_t ldy) {
+    const int cpr = R / 32;                        // 32-byte chunks per output row
+    const int64_t total = (int64_t)F * ldy * cpr;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(q % cpr);
+        const int64_t row = q / cpr;               // f * ldy + t
+        const int t = (int)(row % ldy);
+        const int f = (int)(row / ldy);
+        uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+        if (t < T && 16 * c < N) {
+            const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(frame + ((size_t)t * F + f) * N + 16 * c));
+            dev::expand16_e5m2(v, lo, hi);
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(y + row * R + 32 * c);
+        __stcs(dst, lo);
+        __stcs(dst + 1, hi);
+    }
+}
+
 // ----------------------------------------------------------------------------- epilogue
 
 // Drains 32 TMEM columns (16 column pairs j) of this thread's lane (one row of G) and writes the
 // 8 complex visibilities this thread owns: even lanes (row 2i) take the first 8 j, odd lanes
 // (row 2i+1) the last 8; each obtains the other row's two values per j from its lane partner.
-__device__ __forceinline__ void drain_chunk(uint32_t taddr, int32_t *__restrict__ vis_f, int N, int i,
-                                            bool odd, int j0, bool add) {
+// kScaled: the operand carries 16*Re, so G[re,re] = 256 x, G[re,im] = G[im,re] = 16 x.
+template <bool kScaled>
+__device__ __forceinline__ void drain_chunk(uint32_t taddr, int32_t *__restrict__ vis_f, int N, int i, bool odd,
+                                            int j0, bool add) {
     uint32_t r[32];
     dev::tmem_ld_32x32b_x32(taddr, r);
     dev::tmem_ld_wait();
     int g[32];
+    const float s_even = kScaled ? (odd ? 1.0f / 16.0f : 1.0f / 256.0f) : 1.0f;   // column 2j (re)
+    const float s_odd = kScaled ? (odd ? 1.0f : 1.0f / 16.0f) : 1.0f;             // column 2j+1 (im)
 #pragma unroll
-    for (int k = 0; k < 32; ++k) g[k] = __float2int_rn(__uint_as_float(r[k]));
+    for (int k = 0; k < 16; ++k) {
+        g[2 * k] = __float2int_rn(__uint_as_float(r[2 * k]) * s_even);
+        g[2 * k + 1] = __float2int_rn(__uint_as_float(r[2 * k + 1]) * s_odd);
+    }
     int vr[8], vi[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -201,28 +252,58 @@ __device__ __forceinline__ void drain_chunk(uint32_t taddr, int32_t *__restrict_
 
 // ----------------------------------------------------------------------------- GEMM kernel
 
-__global__ void __launch_bounds__(kThreads, 1) correlate_kernel(const __grid_constant__ Params p) {
+template <int kEngine>
+struct Cfg {
+    static constexpr bool kFused = kEngine == kFusedMN;
+    static constexpr bool kMN = kEngine != kUnpackedK;
+    static constexpr int kThreads = kFused ? 192 + 32 * kConvWarps : 192;
+};
+
+template <int kEngine>
+__global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(const __grid_constant__ Params p) {
+    using C = Cfg<kEngine>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
-    uint64_t *full = bars;                       // [kStages] TMA -> MMA
-    uint64_t *empty = bars + kStages;            // [kStages] MMA -> TMA
-    uint64_t *acc_full = bars + 2 * kStages;     // MMA -> epilogue
-    uint64_t *acc_empty = acc_full + 1;          // epilogue -> MMA
-    uint64_t *done = acc_full + 2;               // teardown
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    const int op_stage_bytes = p.slots * kOpSlotBytes;
+    const int pk_stage_bytes = p.slots * kPkSlotBytes;
+    uint8_t *op_ring = smem;
+    uint8_t *pk_ring = smem + p.op_stages * op_stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(pk_ring + (C::kFused ? p.pk_stages * pk_stage_bytes : 0));
+    uint64_t *op_full = bars;                       // [op_stages] operand ready (TMA or converters)
+    uint64_t *op_empty = op_full + p.op_stages;     // [op_stages] MMA done reading
+    uint64_t *pk_full = op_empty + p.op_stages;     // [pk_stages] packed tile landed (fused)
+    uint64_t *pk_empty = pk_full + p.pk_stages;     // [pk_stages] packed tile consumed (fused)
+    uint64_t *acc_full = pk_empty + p.pk_stages;    // [2] accumulator ready for the epilogue
+    uint64_t *acc_empty = acc_full + 2;             // [2] accumulator drained
+    uint64_t *item_full = acc_empty + 2;            // [kItemRing]
+    uint64_t *item_empty = item_full + kItemRing;   // [kItemRing]
+    uint64_t *done = item_empty + kItemRing;
+    int *item_ring = reinterpret_cast<int *>(done + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(item_ring + kItemRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t smem_base = dev::smem_u32(smem);
+    const uint32_t op_base = dev::smem_u32(op_ring);
+    const uint32_t pk_base = dev::smem_u32(pk_ring);
+    const int n_item_consumers = 1 + 4 + (C::kFused ? kConvWarps : 0);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            dev::mbar_init(&full[s], 1);
-            dev::mbar_init(&empty[s], 1);
+        for (int s = 0; s < p.op_stages; ++s) {
+            dev::mbar_init(&op_full[s], C::kFused ? kConvWarps : 1);
+            dev::mbar_init(&op_empty[s], 1);
         }
-        dev::mbar_init(acc_full, 1);
-        dev::mbar_init(acc_empty, 4);
+        for (int s = 0; s < p.pk_stages; ++s) {
+            dev::mbar_init(&pk_full[s], 1);
+            dev::mbar_init(&pk_empty[s], kConvWarps);
+        }
+        for (int a = 0; a < 2; ++a) {
+            dev::mbar_init(&acc_full[a], 1);
+            dev::mbar_init(&acc_empty[a], 4);
+        }
+        for (int s = 0; s < kItemRing; ++s) {
+            dev::mbar_init(&item_full[s], 1);
+            dev::mbar_init(&item_empty[s], n_item_consumers);
+        }
         dev::mbar_init(done, 1);
         *abort_flag = 0;
         dev::fence_mbar_init();
@@ -253,97 +334,189 @@ __global__ void __launch_bounds__(kThreads, 1) correlate_kernel(const __grid_con
         }
     };
 
+    // Next work item for a consumer role (one call per warp, or by the single MMA thread):
+    // returns the item index, -1 when the list is exhausted, -2 on abort.
+    uint32_t islot = 0, iphase = 0;
+    auto next_item = [&](bool warp_role) -> int {
+        if (!wait(&item_full[islot], iphase)) return -2;
+        const int g = *reinterpret_cast<volatile int *>(&item_ring[islot]);
+        if (warp_role) __syncwarp();
+        if (!warp_role || lane == 0) dev::mbar_arrive(&item_empty[islot]);
+        if (++islot == kItemRing) { islot = 0; iphase ^= 1; }
+        return g;
+    };
+
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------------------------------------------------------- TMA producer
-            uint32_t stage = 0, phase = 0;
-            uint32_t issued = 0, issued_parity = 0;   // per-stage bit masks
+            // ---------------------------------------------------------------- scheduler + TMA producer
+            uint32_t s = 0, ph = 0;                 // op ring (unpacked) or packed ring (fused)
+            uint32_t pslot = 0, pphase = 0;         // item ring
+            uint32_t issued = 0, issued_parity = 0;
+            const int n_stages = C::kFused ? p.pk_stages : p.op_stages;
+            uint64_t *full = C::kFused ? pk_full : op_full;
+            uint64_t *empty = C::kFused ? pk_empty : op_empty;
             bool ok = true;
-            for (int g = blockIdx.x; g < p.n_items && ok; g += gridDim.x) {
+            while (ok) {
+                if (!wait(&item_empty[pslot], pphase ^ 1)) break;
+                int g = atomicAdd(p.counter, 1);
+                if (g >= p.n_items) g = -1;
+                item_ring[pslot] = g;
+                dev::mbar_arrive(&item_full[pslot]);
+                if (++pslot == kItemRing) { pslot = 0; pphase ^= 1; }
+                if (g < 0) break;
                 const Item it = decode_item(p, g);
                 const Job &jb = p.jobs[it.job];
-                int blk[4];
-                int nblk = it.w;
-                for (int c = 0; c < it.w; ++c) blk[c] = it.cb0 + c;
-                if (it.rb < it.cb0) blk[nblk++] = it.rb;
+                const uint32_t tx = C::kFused ? it.nblk * jb.pw * kKt : it.nblk * kOpSlotBytes;
                 for (int kt = 0; kt < jb.k_tiles; ++kt) {
-                    if (!wait(&empty[stage], phase ^ 1)) { ok = false; break; }
-                    dev::mbar_arrive_expect_tx(&full[stage], nblk * kTileBytes);
-                    for (int b = 0; b < nblk; ++b)
-                        dev::tma_load_3d(smem_base + stage * kStageBytes + b * kTileBytes, &jb.tmap, &full[stage],
-                                         kt * kKt, blk[b] * kBlk, it.f);
-                    issued |= 1u << stage;
-                    issued_parity = (issued_parity & ~(1u << stage)) | (phase << stage);
-                    if (++stage == kStages) { stage = 0; phase ^= 1; }
+                    if (!wait(&empty[s], ph ^ 1)) { ok = false; break; }
+                    dev::mbar_arrive_expect_tx(&full[s], tx);
+                    for (int b = 0; b < it.nblk; ++b) {
+                        if (C::kFused)
+                            dev::tma_load_3d(pk_base + s * pk_stage_bytes + b * kPkSlotBytes, &jb.tmap, &full[s],
+                                             it.blk[b] * 64, it.f, kt * kKt);
+                        else if (C::kMN)
+                            dev::tma_load_3d(op_base + s * op_stage_bytes + b * kOpSlotBytes, &jb.tmap, &full[s],
+                                             it.blk[b] * kBlk, kt * kKt, it.f);
+                        else
+                            dev::tma_load_3d(op_base + s * op_stage_bytes + b * kOpSlotBytes, &jb.tmap, &full[s],
+                                             kt * kKt, it.blk[b] * kBlk, it.f);
+                    }
+                    issued |= 1u << s;
+                    issued_parity = (issued_parity & ~(1u << s)) | (ph << s);
+                    if (++s == (uint32_t)n_stages) { s = 0; ph ^= 1; }
                 }
             }
-            // copies still in flight land before the CTA exits
-            for (int s = 0; s < kStages; ++s)
-                if (issued & (1u << s)) dev::mbar_wait(&full[s], (issued_parity >> s) & 1u, p.limit_ns);
+            for (int q = 0; q < n_stages; ++q)
+                if (issued & (1u << q)) dev::mbar_wait(&full[q], (issued_parity >> q) & 1u, p.limit_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------------------- MMA issuer
-            constexpr uint32_t idesc = dev::idesc_e5m2_f32(kBlk, kBlk);
-            uint32_t stage = 0, phase = 0, acc_phase = 0;
+            uint32_t s = 0, ph = 0;
+            uint32_t acc = 0, acc_ph[2] = {0, 0};
             bool ok = true;
-            for (int g = blockIdx.x; g < p.n_items && ok; g += gridDim.x) {
+            while (ok) {
+                const int g = next_item(false);
+                if (g < 0) break;
                 const Item it = decode_item(p, g);
                 const Job &jb = p.jobs[it.job];
-                const int a_slot = it.rb < it.cb0 ? it.w : 0;
                 for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles) {
                     const int k1 = min(jb.k_tiles, k0 + p.k_flush_tiles);
-                    if (!wait(acc_empty, acc_phase ^ 1)) { ok = false; break; }
+                    if (!wait(&acc_empty[acc], acc_ph[acc] ^ 1)) { ok = false; break; }
                     dev::tc_fence_after();
+                    const uint32_t d0 = tmem + acc * 256u;
                     for (int kt = k0; kt < k1; ++kt) {
-                        if (!wait(&full[stage], phase)) { ok = false; break; }
+                        if (!wait(&op_full[s], ph)) { ok = false; break; }
                         dev::tc_fence_after();
-                        const uint32_t sb = smem_base + stage * kStageBytes;
-                        const uint64_t a0 = dev::sdesc_k_sw128(sb + a_slot * kTileBytes);
-                        for (int c = 0; c < it.w; ++c) {
-                            const uint64_t b0 = dev::sdesc_k_sw128(sb + c * kTileBytes);
+                        const uint32_t sb = op_base + s * op_stage_bytes;
 #pragma unroll
-                            for (int kk = 0; kk < kKt / 32; ++kk)   // K = 32 bytes per MMA: +2 in addr>>4
-                                dev::mma_f8f6f4(tmem + c * kBlk, a0 + 2 * kk, b0 + 2 * kk, idesc,
-                                                (kt > k0 || kk > 0) ? 1u : 0u);
+                        for (int kk = 0; kk < kKt / 32; ++kk) {
+                            const uint32_t accum = (kt > k0 || kk > 0) ? 1u : 0u;
+                            for (int c = 0; c < it.w; c += 2) {
+                                const bool wide = c + 1 < it.w;
+                                uint64_t ad, bd;
+                                uint32_t idesc;
+                                if (C::kMN) {   // K step of 32 rows of 128 bytes = 4096 bytes
+                                    ad = dev::sdesc_mn_sw128(sb + it.a_slot * kOpSlotBytes + kk * 4096, kOpSlotBytes);
+                                    bd = dev::sdesc_mn_sw128(sb + c * kOpSlotBytes + kk * 4096, kOpSlotBytes);
+                                    idesc = wide ? dev::idesc_e5m2_f32_mn(128, 256) : dev::idesc_e5m2_f32_mn(128, 128);
+                                } else {        // K step of 32 bytes inside the 128-byte swizzled row
+                                    ad = dev::sdesc_k_sw128(sb + it.a_slot * kOpSlotBytes + kk * 32);
+                                    bd = dev::sdesc_k_sw128(sb + c * kOpSlotBytes + kk * 32);
+                                    idesc = wide ? dev::idesc_e5m2_f32(128, 256) : dev::idesc_e5m2_f32(128, 128);
+                                }
+                                dev::mma_f8f6f4(d0 + c * kBlk, ad, bd, idesc, accum);
+                            }
                         }
-                        dev::tc_commit(&empty[stage]);
-                        if (++stage == kStages) { stage = 0; phase ^= 1; }
+                        dev::tc_commit(&op_empty[s]);
+                        if (++s == (uint32_t)p.op_stages) { s = 0; ph ^= 1; }
                     }
                     if (!ok) break;
-                    dev::tc_commit(acc_full);
-                    acc_phase ^= 1;
+                    dev::tc_commit(&acc_full[acc]);
+                    acc_ph[acc] ^= 1;
+                    acc = (acc + 1) % p.n_acc;
                 }
             }
             dev::tc_commit(done);
             dev::mbar_wait(done, 0, p.limit_ns);
         }
-    } else {
+    } else if (warp < 6) {
         // -------------------------------------------------------------------- epilogue warps
         const int q = warp & 3;                 // TMEM lane quarter this warp may access
-        const int m = q * 32 + lane;            // row of the 128x128 tile
+        const int m = q * 32 + lane;            // row of the 128-row tile
         const bool odd = (m & 1) != 0;
-        uint32_t acc_phase = 0;
+        uint32_t acc = 0, acc_ph[2] = {0, 0};
         bool ok = true;
-        for (int g = blockIdx.x; g < p.n_items && ok; g += gridDim.x) {
+        while (ok) {
+            const int g = next_item(true);
+            if (g < 0) break;
             const Item it = decode_item(p, g);
             const Job &jb = p.jobs[it.job];
             const int N = jb.n_inputs;
             const int i = (it.rb * kBlk + m) >> 1;
             int32_t *vis_f = jb.vis + (size_t)it.f * (size_t)npairs(N) * 2;
             for (int k0 = 0; k0 < jb.k_tiles; k0 += p.k_flush_tiles) {
-                if (!wait(acc_full, acc_phase)) { ok = false; break; }
+                if (!wait(&acc_full[acc], acc_ph[acc])) { ok = false; break; }
                 dev::tc_fence_after();
                 const bool add = jb.accumulate || k0 > 0;
+                const uint32_t tb = tmem + acc * 256u + (uint32_t(q * 32) << 16);
                 for (int c = 0; c < it.w; ++c)
 #pragma unroll 1
                     for (int ch = 0; ch < kBlk / 32; ++ch)
-                        drain_chunk(tmem + (uint32_t(q * 32) << 16) + c * kBlk + ch * 32, vis_f, N, i, odd,
-                                    ((it.cb0 + c) * kBlk + ch * 32) >> 1, add);
+                        drain_chunk<C::kMN>(tb + c * kBlk + ch * 32, vis_f, N, i, odd,
+                                            ((it.cb0 + c) * kBlk + ch * 32) >> 1, add);
                 dev::tc_fence_before();
                 __syncwarp();
-                if (lane == 0) dev::mbar_arrive(acc_empty);
-                acc_phase ^= 1;
+                if (lane == 0) dev::mbar_arrive(&acc_empty[acc]);
+                acc_ph[acc] ^= 1;
+                acc = (acc + 1) % p.n_acc;
+            }
+        }
+    } else if (C::kFused) {
+        // -------------------------------------------------------------------- converter warps
+        // Packed tile [128 t][pw bytes] -> MN-major operand rows: row t of block b holds the 128
+        // codes (16 Re, Im) of inputs 64*blk .. 64*blk+63 at sample t, 16-byte chunks swizzled
+        // as chunk ^ (t & 7) (the 128-byte swizzle the MMA descriptor names).
+        const int ctid = threadIdx.x - 192;
+        uint32_t ps = 0, pph = 0, os = 0, oph = 0;
+        bool ok = true;
+        while (ok) {
+            const int g = next_item(true);
+            if (g < 0) break;
+            const Item it = decode_item(p, g);
+            const Job &jb = p.jobs[it.job];
+            const int pw = jb.pw;
+            for (int kt = 0; kt < jb.k_tiles; ++kt) {
+                if (!wait(&pk_full[ps], pph)) { ok = false; break; }
+                if (!wait(&op_empty[os], oph ^ 1)) { ok = false; break; }
+                const uint32_t pk = pk_base + ps * pk_stage_bytes;
+                const uint32_t op = op_base + os * op_stage_bytes;
+                for (int task = ctid; task < it.nblk * 512; task += 32 * kConvWarps) {
+                    const int b = task >> 9, r = task & 511;
+                    const int t = r >> 2, c = r & 3;
+                    uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+                    if (c * 16 < pw) {
+                        uint4 v;
+                        asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                                     : "r"(pk + b * kPkSlotBytes + t * pw + c * 16));
+                        dev::expand16_e5m2(v, lo, hi);
+                    }
+                    const uint32_t row = op + b * kOpSlotBytes + t * 128;
+                    const uint32_t sw = t & 7;
+                    asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                                 ::"r"(row + (((2 * c) ^ sw) << 4)), "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w));
+                    asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                                 ::"r"(row + (((2 * c + 1) ^ sw) << 4)), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
+                }
+                dev::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                    dev::mbar_arrive(&pk_empty[ps]);
+                    dev::mbar_arrive(&op_full[os]);
+                }
+                if (++ps == (uint32_t)p.pk_stages) { ps = 0; pph ^= 1; }
+                if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
             }
         }
     }
@@ -362,13 +535,13 @@ struct JobGeom {
     size_t y_bytes;
 };
 
-static JobGeom geom(const xe_shape &s) {
+static JobGeom geom(const xe_shape &s, int engine) {
     JobGeom g;
     g.R = (int)round_up(2 * (int64_t)s.n_inputs, kBlk);
     g.nb = g.R / kBlk;
     g.ldy = round_up(std::max<int64_t>(s.n_time, 1), kKt);
     g.k_tiles = (int)((s.n_time + kKt - 1) / kKt);
-    g.y_bytes = (size_t)round_up((int64_t)s.n_chan * g.R * g.ldy, 1024);
+    g.y_bytes = engine == kFusedMN ? 0 : (size_t)round_up((int64_t)s.n_chan * g.R * g.ldy, 1024);
     return g;
 }
 
@@ -379,9 +552,18 @@ static int check_job(const xe_shape &s, const void *frame, const void *vis) {
     return XE_OK;
 }
 
+static int engine_of(int api_engine) {
+    switch (api_engine) {
+        case XE_ENGINE_UNPACKED: return kUnpackedMN;
+        case XE_ENGINE_FUSED: return kFusedMN;
+        case XE_ENGINE_UNPACKED_K: return kUnpackedK;
+        default: return -1;
+    }
+}
+
 static void resolve_tune(const xe_tune *t, xe_tune &out) {
-    out.engine = XE_ENGINE_UNPACKED;
-    out.max_strip = 4;
+    out.engine = XE_ENGINE_FUSED;
+    out.max_strip = 2;
     out.k_flush = kDefaultKFlush;
     out.n_ctas = 0;
     if (!t) return;
@@ -392,24 +574,49 @@ static void resolve_tune(const xe_tune *t, xe_tune &out) {
 }
 
 static int check_tune(const xe_tune &t) {
-    if (t.engine != XE_ENGINE_UNPACKED) return XE_EINVAL;
+    if (engine_of(t.engine) < 0) return XE_EINVAL;
     if (t.max_strip < 1 || t.max_strip > 4) return XE_EINVAL;
     if (t.k_flush < kKt || t.k_flush % kKt || t.k_flush > (1 << 18)) return XE_EINVAL;
     if (t.n_ctas < 0) return XE_EINVAL;
     return XE_OK;
 }
 
-static size_t batched_ws(const xe_job *jobs, int n) {
-    size_t b = 1024;     // slack: the operand base is aligned up to 1 KiB inside the workspace
-    for (int j = 0; j < n; ++j) b += geom(jobs[j].s).y_bytes;
+static constexpr size_t kWsHeader = 1024;   // work-item counter; operands start 1 KiB in
+
+static size_t batched_ws(const xe_job *jobs, int n, int engine) {
+    size_t b = kWsHeader + 1024;   // + slack: the workspace is aligned up to 1 KiB inside
+    for (int j = 0; j < n; ++j) b += geom(jobs[j].s, engine).y_bytes;
     return b;
 }
 
-static int launch_unpack(const uint8_t *frame, const xe_shape &s, uint8_t *y, int64_t ldy, cudaStream_t st) {
+static int launch_unpack(int engine, const uint8_t *frame, const xe_shape &s, uint8_t *y, int64_t ldy,
+                         cudaStream_t st) {
     const int R = (int)round_up(2 * (int64_t)s.n_inputs, kBlk);
-    dim3 grid((unsigned)(ldy / 128), (unsigned)(R / 128), (unsigned)s.n_chan);
-    if (grid.x == 0 || grid.z > 65535u) return XE_EINVAL;
-    unpack_kernel<<<grid, 256, 0, st>>>(frame, y, s.n_inputs, s.n_chan, s.n_time, R, ldy);
+    if (engine == kUnpackedK) {
+        dim3 grid((unsigned)(ldy / 128), (unsigned)(R / 128), (unsigned)s.n_chan);
+        if (grid.x == 0 || grid.z > 65535u) return XE_EINVAL;
+        unpack_k_kernel<<<grid, 256, 0, st>>>(frame, y, s.n_inputs, s.n_chan, s.n_time, R, ldy);
+    } else {
+        const int64_t chunks = (int64_t)s.n_chan * ldy * (R / 32);
+        const int blocks = (int)std::min<int64_t>((chunks + 255) / 256, (int64_t)sm_count() * 16);
+        unpack_mn_kernel<<<blocks, 256, 0, st>>>(frame, y, s.n_inputs, s.n_chan, s.n_time, R, ldy);
+    }
+    XE_TRY_CUDA(cudaGetLastError());
+    return XE_OK;
+}
+
+template <int kEngine>
+static int launch_gemm(const Params &hp, int ctas, int smem, cudaStream_t st) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    XE_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev >= 64) return XE_EINVAL;
+    if (!attr_set[dev]) {
+        XE_TRY_CUDA(cudaFuncSetAttribute(correlate_kernel<kEngine>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemMax));
+        attr_set[dev] = true;
+    }
+    correlate_kernel<kEngine><<<ctas, Cfg<kEngine>::kThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
@@ -420,9 +627,10 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     xe_tune tune;
     resolve_tune(tune_in, tune);
     if (int e = check_tune(tune)) return e;
+    const int engine = engine_of(tune.engine);
     for (int j = 0; j < n_jobs; ++j)
         if (int e = check_job(jobs[j].s, jobs[j].frame, jobs[j].vis)) return e;
-    if (ws_bytes < batched_ws(jobs, n_jobs) || (!ws && batched_ws(jobs, n_jobs))) return XE_ENOMEM;
+    if (!ws || ws_bytes < batched_ws(jobs, n_jobs, engine)) return XE_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) & 15) return XE_EINVAL;
     int *status = status_word();
     if (!status) return XE_ECUDA;
@@ -431,11 +639,13 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
     std::memset(&hp, 0, sizeof(hp));
-    uint8_t *ybase = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
+    int *counter = reinterpret_cast<int *>(base);
+    uint8_t *ybase = base + kWsHeader;
     int items = 0, nj = 0;
     for (int j = 0; j < n_jobs; ++j) {
         const xe_shape &s = jobs[j].s;
-        const JobGeom g = geom(s);
+        const JobGeom g = geom(s, engine);
         uint8_t *y = ybase;
         ybase += g.y_bytes;
         if (s.n_time == 0) {     // empty integration: V = 0
@@ -443,14 +653,33 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
                 XE_TRY_CUDA(cudaMemsetAsync(jobs[j].vis, 0, (size_t)s.n_chan * npairs(s.n_inputs) * 8, st));
             continue;
         }
-        if (int e = launch_unpack(jobs[j].frame, s, y, g.ldy, st)) return e;
         Job &d = hp.jobs[nj++];
-        const uint64_t dims[3] = {(uint64_t)g.ldy, (uint64_t)g.R, (uint64_t)s.n_chan};
-        const uint64_t strides[2] = {(uint64_t)g.ldy, (uint64_t)g.ldy * g.R};
-        const uint32_t box[3] = {kKt, kBlk, 1};
-        if (encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, y, dims, strides, box,
-                         CU_TENSOR_MAP_SWIZZLE_128B) != XE_OK)
-            return XE_EINVAL;
+        int enc;
+        if (engine == kFusedMN) {
+            const uint32_t pw = (uint32_t)std::min(64, s.n_inputs);
+            const uint64_t dims[3] = {(uint64_t)s.n_inputs, (uint64_t)s.n_chan, (uint64_t)s.n_time};
+            const uint64_t strides[2] = {(uint64_t)s.n_inputs, (uint64_t)s.n_inputs * s.n_chan};
+            const uint32_t box[3] = {pw, 1, kKt};
+            enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(jobs[j].frame), dims,
+                               strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
+            d.pw = (int)pw;
+        } else {
+            if (int e = launch_unpack(engine, jobs[j].frame, s, y, g.ldy, st)) return e;
+            const uint32_t box[3] = {kKt, kBlk, 1};
+            if (engine == kUnpackedMN) {
+                const uint64_t dims[3] = {(uint64_t)g.R, (uint64_t)g.ldy, (uint64_t)s.n_chan};
+                const uint64_t strides[2] = {(uint64_t)g.R, (uint64_t)g.R * g.ldy};
+                enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, y, dims, strides, box,
+                                   CU_TENSOR_MAP_SWIZZLE_128B);
+            } else {
+                const uint64_t dims[3] = {(uint64_t)g.ldy, (uint64_t)g.R, (uint64_t)s.n_chan};
+                const uint64_t strides[2] = {(uint64_t)g.ldy, (uint64_t)g.ldy * g.R};
+                enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, y, dims, strides, box,
+                                   CU_TENSOR_MAP_SWIZZLE_128B);
+            }
+            d.pw = 64;
+        }
+        if (enc != XE_OK) return XE_EINVAL;
         d.vis = jobs[j].vis;
         d.n_inputs = s.n_inputs;
         d.n_chan = s.n_chan;
@@ -469,20 +698,29 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     hp.n_items = items;
     hp.max_strip = tune.max_strip;
     hp.k_flush_tiles = tune.k_flush / kKt;
+    hp.slots = tune.max_strip == 1 ? 2 : (tune.max_strip == 2 ? 3 : 4);
+    hp.n_acc = tune.max_strip <= 2 ? 2 : 1;
     hp.status = status;
+    hp.counter = counter;
     hp.limit_ns = wait_limit_ns();
-
-    static bool attr_set[64] = {};
-    int dev = 0;
-    XE_TRY_CUDA(cudaGetDevice(&dev));
-    if (dev < 64 && !attr_set[dev]) {
-        XE_TRY_CUDA(cudaFuncSetAttribute(correlate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-        attr_set[dev] = true;
+    const int bar_bytes = 1024;
+    const int avail = kSmemMax - 1024 - bar_bytes;
+    if (engine == kFusedMN) {
+        hp.pk_stages = 3;
+        hp.op_stages = std::min(4, (avail - hp.pk_stages * hp.slots * kPkSlotBytes) / (hp.slots * kOpSlotBytes));
+    } else {
+        hp.pk_stages = 0;
+        hp.op_stages = std::min(6, avail / (hp.slots * kOpSlotBytes));
     }
+    if (hp.op_stages < 2) return XE_EINVAL;
+    const int smem = 1024 + hp.op_stages * hp.slots * kOpSlotBytes + hp.pk_stages * hp.slots * kPkSlotBytes + bar_bytes;
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
-    correlate_kernel<<<ctas, kThreads, kSmemBytes, st>>>(hp);
-    XE_TRY_CUDA(cudaGetLastError());
-    return XE_OK;
+    XE_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    switch (engine) {
+        case kUnpackedK: return launch_gemm<kUnpackedK>(hp, ctas, smem, st);
+        case kUnpackedMN: return launch_gemm<kUnpackedMN>(hp, ctas, smem, st);
+        default: return launch_gemm<kFusedMN>(hp, ctas, smem, st);
+    }
 }
 
 }  // namespace corr
@@ -495,12 +733,13 @@ extern "C" {
 int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *stream) {
     if (!valid_shape(s) || !frame || !y || ldy < std::max(s.n_time, 1) || ldy % 128) return XE_EINVAL;
     if ((reinterpret_cast<uintptr_t>(frame) & 15) || (reinterpret_cast<uintptr_t>(y) & 15)) return XE_EINVAL;
-    return corr::launch_unpack(frame, s, y, ldy, static_cast<cudaStream_t>(stream));
+    return corr::launch_unpack(corr::kUnpackedMN, frame, s, y, ldy, static_cast<cudaStream_t>(stream));
 }
 
 size_t xe_correlate_workspace_size(xe_shape s) {
     if (!valid_shape(s)) return 0;
-    return corr::geom(s).y_bytes + 1024;
+    xe_job j{nullptr, nullptr, s, 0};
+    return corr::batched_ws(&j, 1, corr::engine_of(XE_ENGINE_FUSED));
 }
 
 int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate, void *ws, size_t ws_bytes,
@@ -509,11 +748,15 @@ int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate,
     return corr::run_batched(&j, 1, nullptr, ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 
-size_t xe_correlate_batched_workspace_size(const xe_job *jobs, int32_t n_jobs, const xe_tune *) {
+size_t xe_correlate_batched_workspace_size(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune) {
     if (!jobs || n_jobs < 1 || n_jobs > XE_MAX_JOBS) return 0;
     for (int j = 0; j < n_jobs; ++j)
         if (!valid_shape(jobs[j].s)) return 0;
-    return corr::batched_ws(jobs, n_jobs);
+    xe_tune t;
+    corr::resolve_tune(tune, t);
+    const int e = corr::engine_of(t.engine);
+    if (e < 0) return 0;
+    return corr::batched_ws(jobs, n_jobs, e);
 }
 
 int xe_correlate_batched(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune, void *ws, size_t ws_bytes,

@@ -162,6 +162,25 @@ __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// Shared-memory matrix descriptor of an MN-major operand tile with the 128-byte swizzle: one row
+// of 128 bytes (128 values along M or N) per K index, 8-row (1024-byte) swizzle atoms stacked
+// along K (stride byte offset 1024); `lbo` is the byte distance between consecutive 128-value
+// atoms along M/N (used when the operand spans more than 128 values, e.g. N = 256).
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t lbo) {
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+    d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+    d |= static_cast<uint64_t>(1024u >> 4) << 32;
+    d |= static_cast<uint64_t>(1u) << 46;
+    d |= static_cast<uint64_t>(2u) << 61;
+    return d;
+}
+
+// Same as idesc_e5m2_f32 with both operands MN-major (transpose bits 15 and 16 set).
+__host__ __device__ constexpr uint32_t idesc_e5m2_f32_mn(uint32_t m, uint32_t n) {
+    return idesc_e5m2_f32(m, n) | (1u << 15) | (1u << 16);
+}
+
 // ------------------------------------------------------------------ 4-bit -> E5M2
 
 // Four packed 4-bit two's-complement values (one per byte, in bits 0-3 of each byte) to four
@@ -178,6 +197,35 @@ __device__ __forceinline__ uint32_t nibbles_to_e5m2(uint32_t lo_nibbles) {
     asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d01) : "r"(h01), "r"(k));
     asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(d23) : "r"(h23), "r"(k));
     return __byte_perm(d01, d23, 0x7531);
+}
+
+// Four packed samples (bytes re<<4 | im, 4-bit two's complement) -> eight E5M2 codes in sample
+// order, each sample as (16*re, im). Per half-precision lane: (x & 0x000F) ^ 0x6408 has the bits of
+// 1024 + (im ^ 8) = 1032 + im, and (x & 0x00F0) ^ 0x6480 those of 1024 + 16*(re ^ 8) = 1152 + 16*re;
+// subtracting 1032 resp. 1152 is exact and leaves im resp. 16*re, whose low bytes are zero, so
+// the high bytes are their E5M2 codes. 13 integer/half2 operations for 8 codes.
+__device__ __forceinline__ void expand4_e5m2(uint32_t x, uint32_t &w0, uint32_t &w1) {
+    const uint32_t x8 = x >> 8;
+    uint32_t im02 = (x & 0x000F000Fu) ^ 0x64086408u;
+    uint32_t im13 = (x8 & 0x000F000Fu) ^ 0x64086408u;
+    uint32_t re02 = (x & 0x00F000F0u) ^ 0x64806480u;
+    uint32_t re13 = (x8 & 0x00F000F0u) ^ 0x64806480u;
+    const uint32_t k_im = 0x64086408u, k_re = 0x64806480u;
+    asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(im02) : "r"(k_im));
+    asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(im13) : "r"(k_im));
+    asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re02) : "r"(k_re));
+    asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re13) : "r"(k_re));
+    const uint32_t re = __byte_perm(re02, re13, 0x7351);   // re0 re1 re2 re3
+    const uint32_t im = __byte_perm(im02, im13, 0x7351);   // im0 im1 im2 im3
+    w0 = __byte_perm(re, im, 0x5140);                      // re0 im0 re1 im1
+    w1 = __byte_perm(re, im, 0x7362);                      // re2 im2 re3 im3
+}
+
+__device__ __forceinline__ void expand16_e5m2(const uint4 &in, uint4 &lo, uint4 &hi) {
+    expand4_e5m2(in.x, lo.x, lo.y);
+    expand4_e5m2(in.y, lo.z, lo.w);
+    expand4_e5m2(in.z, hi.x, hi.y);
+    expand4_e5m2(in.w, hi.z, hi.w);
 }
 
 }  // namespace dev

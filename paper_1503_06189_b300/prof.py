@@ -41,8 +41,17 @@ def main(argv=None):
         tune = dict(engine=a.engine, max_strip=a.max_strip, k_flush=0, n_ctas=0)
         jobs = [(frame, vis, s, False)]
         ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device=dev)
-        for _ in range(a.iters):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.iters)]
+        for e0, e1 in evs:
+            e0.record()
             xe.xe_correlate_batched(jobs, ws, tune)
+            e1.record()
+        torch.cuda.synchronize()
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        best = min(ms[1:] if len(ms) > 1 else ms)
+        cmac = F * P * T
+        print(f"correlate engine={a.engine} max_strip={a.max_strip} N={N} F={F} T={T}: best {best:.4f} ms, "
+              f"{cmac / best / 1e9:.3f} TCMAC/s, {8 * cmac / best / 1e9:.1f} T int-op/s", flush=True)
     elif a.op == "assemble":
         import synth
         pk = synth.packetize_torch(frame, 0, 1)

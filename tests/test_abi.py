@@ -36,5 +36,9 @@ def test_host_only_calls():
     assert "overflow" in xe.xe_strerror(xe.XE_EOVERFLOW) or "int32" in xe.xe_strerror(xe.XE_EOVERFLOW)
     assert xe.xe_correlate_workspace_size(xe.Shape(20, 1, 128)) == 0          # N % 16 != 0
     s = xe.Shape(256, 64, 16384)
-    assert xe.xe_correlate_workspace_size(s) >= 64 * 512 * 16384
+    assert 0 < xe.xe_correlate_workspace_size(s) <= 4096          # fused default: work counter only
+    jobs = [(0, 0, s, False)]
+    unpacked = xe.xe_correlate_batched_workspace_size(jobs, dict(engine=xe.XE_ENGINE_UNPACKED, max_strip=0,
+                                                                 k_flush=0, n_ctas=0))
+    assert unpacked >= 64 * 512 * 16384                           # + the E5M2 operand in HBM
     assert xe.xe_assemble_workspace_size(xe.Shape(256, 1024, 4096)) == 1024 * 128 * 4

@@ -28,7 +28,7 @@ def assert_vis_equal(got, want):
 def test_unpack_codes(N, F, T):
     fr = synth.uniform_frame(N, F, T, 100 + N + T)
     want, R, ldy = X.e5m2_codes(fr)
-    y = torch.full((F, R, ldy), 0x5A, dtype=torch.uint8, device="cuda")
+    y = torch.full((F, ldy, R), 0x5A, dtype=torch.uint8, device="cuda")
     xe.xe_unpack(X.dev(fr), xe.Shape(N, F, T), y, ldy)
     np.testing.assert_array_equal(y.cpu().numpy(), want)
 
@@ -108,13 +108,35 @@ def test_correlate_workspace_too_small():
     assert e.value.status == xe.XE_ENOMEM
 
 
-@pytest.mark.parametrize("max_strip,k_flush", [(1, 128), (2, 256), (3, 384), (4, 128), (4, 0)])
-def test_correlate_tunings_agree(max_strip, k_flush):
-    """Every strip width and TMEM drain interval gives the same bits."""
+ENGINES = [xe.XE_ENGINE_FUSED, xe.XE_ENGINE_UNPACKED, xe.XE_ENGINE_UNPACKED_K]
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("max_strip,k_flush", [(1, 128), (2, 256), (3, 384), (4, 128), (2, 0), (4, 0)])
+def test_correlate_tunings_agree(engine, max_strip, k_flush):
+    """Every engine, strip width and TMEM drain interval gives the same bits."""
     fr = synth.uniform_frame(272, 2, 1000, 9)
     want, _ = oracle.correlate(fr)
-    (got,) = X.correlate_batched([fr], tune=dict(engine=xe.XE_ENGINE_UNPACKED, max_strip=max_strip,
-                                                 k_flush=k_flush, n_ctas=0))
+    (got,) = X.correlate_batched([fr], tune=dict(engine=engine, max_strip=max_strip, k_flush=k_flush, n_ctas=0))
+    assert_vis_equal(got, want)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+@pytest.mark.parametrize("N,F,T", [(16, 3, 200), (48, 2, 256), (80, 2, 300), (256, 4, 1024), (512, 1, 384)])
+def test_correlate_engines_shapes(engine, N, F, T):
+    """Small and ragged N (packed rows narrower than 64 bytes, partial 64-input blocks) per engine."""
+    fr = synth.uniform_frame(N, F, T, 3 * N + T + engine)
+    want, _ = oracle.correlate(fr)
+    (got,) = X.correlate_batched([fr], tune=dict(engine=engine, max_strip=0, k_flush=0, n_ctas=0))
+    assert_vis_equal(got, want)
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_correlate_few_ctas(engine):
+    """Fewer persistent CTAs than work items: each CTA takes many items from the shared counter."""
+    fr = synth.uniform_frame(256, 9, 512, 31)
+    want, _ = oracle.correlate(fr)
+    (got,) = X.correlate_batched([fr], tune=dict(engine=engine, max_strip=0, k_flush=0, n_ctas=3))
     assert_vis_equal(got, want)
 
 
@@ -148,8 +170,9 @@ def test_correlate_pathfinder_frame_sampled():
         want, st = oracle.correlate(host, f, 1)
         assert st == oracle.OK
         assert_vis_equal(vis[f:f + 1], want)
-    (alt,) = X.correlate_batched([fr], tune=dict(engine=xe.XE_ENGINE_UNPACKED, max_strip=2, k_flush=2048, n_ctas=0))
-    assert torch.equal(alt, vis)
+    for engine, ms in ((xe.XE_ENGINE_UNPACKED, 4), (xe.XE_ENGINE_UNPACKED_K, 3), (xe.XE_ENGINE_FUSED, 1)):
+        (alt,) = X.correlate_batched([fr], tune=dict(engine=engine, max_strip=ms, k_flush=2048, n_ctas=0))
+        assert torch.equal(alt, vis), (engine, ms)
 
 
 # ----------------------------------------------------------------------------- A1 assemble

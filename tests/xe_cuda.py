@@ -35,15 +35,16 @@ def correlate_batched(frames, tune=None, accumulate=False):
 
 
 def e5m2_codes(frame):
-    """Expected unpack output [F][R][ldy] of a frame, from numpy's float16 (E5M2 = high byte)."""
+    """Expected unpack output [F][ldy][R] of a frame: per sample t, (16 Re, Im) E5M2 codes of every
+    input in order, zero padded. E5M2 codes taken from numpy's float16 (E5M2 = its high byte)."""
     T, F, N = frame.shape
     b = frame.astype(np.int64)
     re = ((b >> 4) ^ 8) - 8
     im = ((b & 15) ^ 8) - 8
     R = -(-2 * N // 128) * 128
     ldy = -(-max(T, 1) // 128) * 128
-    out = np.zeros((F, R, ldy), np.uint8)
+    out = np.zeros((F, ldy, R), np.uint8)
     code = lambda v: (v.astype(np.float16).view(np.uint16) >> 8).astype(np.uint8)
-    out[:, 0:2 * N:2, :T] = code(re).transpose(1, 2, 0)
-    out[:, 1:2 * N:2, :T] = code(im).transpose(1, 2, 0)
+    out[:, :T, 0:2 * N:2] = code(16 * re).transpose(1, 0, 2)
+    out[:, :T, 1:2 * N:2] = code(im).transpose(1, 0, 2)
     return out, R, ldy
