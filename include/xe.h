@@ -101,9 +101,9 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
 /*
  * Unpack a frame into the tensor-core operand of the correlation (Sec. II-B: the packed 4-bit
  * data cross the host link unpromoted; the promotion happens here, on the device). For channel f
- * and sample t, row t of y holds 2N FP8 E5M2 codes in input order, (16 Re x_n(t), Im x_n(t)) for
- * n = 0..N-1 (the integers are exact in E5M2; the factor 16 is a power of two removed again when
- * the correlation is drained), then zeros up to R.
+ * and sample t, row t of y holds 2N FP8 E5M2 codes in groups of four inputs, (16 Re x_{4g..4g+3},
+ * Im x_{4g..4g+3}) for g = 0..N/4-1 (the integers are exact in E5M2; the factor 16 is a power of
+ * two removed again when the correlation is drained), then zeros up to R.
  *   y      out, uint8 [F][ldy][R] with R = round_up(2N, 128); rows T..ldy-1 are zero.
  *          ldy % 128 == 0 and ldy >= T.
  */

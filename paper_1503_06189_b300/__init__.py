@@ -4,7 +4,8 @@ Argument marshalling only: every step of the hot path runs in libxe's CUDA kerne
 for device memory and streams. The functions keep the C names; tensors are passed as torch CUDA
 tensors (or raw integer device pointers where noted) and shapes as ``Shape(N, F, T)``.
 
-There is no fallback: if libxe.so is missing or fails to load, importing the binding raises.
+There is no fallback: if libxe.so is missing or fails to load, the first call into the binding
+raises ImportError (importing the package alone does not, so that its build module can run).
 """
 from __future__ import annotations
 
@@ -30,9 +31,10 @@ EXPORTED = [
 class XeError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
-        msg = _lib.xe_strerror(status).decode() if _lib is not None else str(status)
-        if status == XE_ECUDA and _lib is not None:
-            msg += f" (cudaError {_lib.xe_last_cuda_error()})"
+        L = lib()
+        msg = L.xe_strerror(status).decode()
+        if status == XE_ECUDA:
+            msg += f" (cudaError {L.xe_last_cuda_error()})"
         super().__init__(f"{what}: {msg} [{status}]")
 
 
@@ -82,11 +84,23 @@ def _load():
     return L
 
 
-_lib = _load()
+_lib = None
 
 
 def lib():
+    """The loaded libxe (loaded on first use; raises ImportError if it is missing)."""
+    global _lib
+    if _lib is None:
+        _lib = _load()
     return _lib
+
+
+class _Lazy:
+    def __getattr__(self, name):
+        return getattr(lib(), name)
+
+
+_L = _Lazy()
 
 
 # ----------------------------------------------------------------------------- marshalling helpers
@@ -124,36 +138,36 @@ def npairs(n: int) -> int:
 # ----------------------------------------------------------------------------- library
 
 def xe_strerror(status: int) -> str:
-    return _lib.xe_strerror(status).decode()
+    return _L.xe_strerror(status).decode()
 
 
 def xe_last_cuda_error() -> int:
-    return _lib.xe_last_cuda_error()
+    return _L.xe_last_cuda_error()
 
 
 def xe_version() -> int:
-    return _lib.xe_version()
+    return _L.xe_version()
 
 
 def xe_device_status(stream=None) -> int:
     v = ctypes.c_int(0)
-    _check(_lib.xe_device_status(ctypes.byref(v), _stream(stream)), "xe_device_status")
+    _check(_L.xe_device_status(ctypes.byref(v), _stream(stream)), "xe_device_status")
     return v.value
 
 
 def xe_selftest_timeout(timeout_ns: int, stream=None):
-    _check(_lib.xe_selftest_timeout(timeout_ns, _stream(stream)), "xe_selftest_timeout")
+    _check(_L.xe_selftest_timeout(timeout_ns, _stream(stream)), "xe_selftest_timeout")
 
 
 # ----------------------------------------------------------------------------- A1
 
 def xe_assemble_workspace_size(shape: Shape) -> int:
-    return _lib.xe_assemble_workspace_size(shape)
+    return _L.xe_assemble_workspace_size(shape)
 
 
 def xe_assemble(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
                 frame, filled, lost, stats, ws, stream=None):
-    _check(_lib.xe_assemble(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(frame),
+    _check(_L.xe_assemble(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(frame),
                             _ptr(filled), _ptr(lost), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)),
            "xe_assemble")
 
@@ -161,15 +175,15 @@ def xe_assemble(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream
 # ----------------------------------------------------------------------------- A2..A4
 
 def xe_unpack(frame, shape: Shape, y, ldy: int, stream=None):
-    _check(_lib.xe_unpack(_ptr(frame), shape, _ptr(y), ldy, _stream(stream)), "xe_unpack")
+    _check(_L.xe_unpack(_ptr(frame), shape, _ptr(y), ldy, _stream(stream)), "xe_unpack")
 
 
 def xe_correlate_workspace_size(shape: Shape) -> int:
-    return _lib.xe_correlate_workspace_size(shape)
+    return _L.xe_correlate_workspace_size(shape)
 
 
 def xe_correlate(frame, shape: Shape, vis, accumulate: bool, ws, stream=None):
-    _check(_lib.xe_correlate(_ptr(frame), shape, _ptr(vis), 1 if accumulate else 0, _ptr(ws), _nbytes(ws),
+    _check(_L.xe_correlate(_ptr(frame), shape, _ptr(vis), 1 if accumulate else 0, _ptr(ws), _nbytes(ws),
                              _stream(stream)), "xe_correlate")
 
 
@@ -190,13 +204,13 @@ def _tune(tune):
 
 def xe_correlate_batched_workspace_size(jobs, tune=None) -> int:
     arr = _jobs(jobs)
-    return _lib.xe_correlate_batched_workspace_size(arr, len(jobs), _tune(tune))
+    return _L.xe_correlate_batched_workspace_size(arr, len(jobs), _tune(tune))
 
 
 def xe_correlate_batched(jobs, ws, tune=None, stream=None):
     """jobs: sequence of (frame, vis, Shape, accumulate)."""
     arr = _jobs(jobs)
-    _check(_lib.xe_correlate_batched(arr, len(jobs), _tune(tune), _ptr(ws), _nbytes(ws), _stream(stream)),
+    _check(_L.xe_correlate_batched(arr, len(jobs), _tune(tune), _ptr(ws), _nbytes(ws), _stream(stream)),
            "xe_correlate_batched")
 
 
@@ -204,5 +218,5 @@ def xe_correlate_batched(jobs, ws, tune=None, stream=None):
 
 def xe_normalize(vis, shape: Shape, t_int: int, lost, out, n_out=None, flag_count=None, flag_pairs=None,
                  stream=None):
-    _check(_lib.xe_normalize(_ptr(vis), shape, t_int, _ptr(lost), _ptr(flag_count), _ptr(flag_pairs), _ptr(out),
+    _check(_L.xe_normalize(_ptr(vis), shape, t_int, _ptr(lost), _ptr(flag_count), _ptr(flag_pairs), _ptr(out),
                              _ptr(n_out), _stream(stream)), "xe_normalize")

@@ -17,8 +17,8 @@
 //   FUSED       no unpack: TMA loads packed [128 t][64 n] byte tiles of the frame and converter
 //               warps expand them in shared memory into the MN-major operand layout.
 // Roles: warp 0 = scheduler + TMA producer, warp 1 = TMEM owner + MMA issuer (one thread),
-// warps 2..5 = epilogue (tcgen05.ld, FP32 -> int32, 2x2 Re/Im combine by shfl.xor, store or
-// accumulate into the packed triangle), warps 6..13 = converters (FUSED only).
+// warps 2..9 = epilogue (tcgen05.ld, FP32 -> int32, 2x2 Re/Im combine by shfl.xor, store or
+// accumulate into the packed triangle), warps 10..17 = converters (FUSED only).
 // Work items (job, channel, strip) are handed out dynamically (one atomic per item), channel by
 // channel, so that the strips of a channel run together and share its data in L2.
 #include <cuda.h>
@@ -108,9 +108,12 @@ __host__ __device__ inline void decode_strip(int s, int nb, int ms, int &rb, int
 
 struct Item {
     int job, f, rb, cb0, w;
-    int nblk, a_slot;
-    int blk[4];
+    int nblk;      // operand blocks per stage: the w B blocks, plus A when it is not among them
+    int a_slot;    // stage slot holding the A block
 };
+
+// Operand block held in stage slot b: the B blocks cb0.. first, then A (off-diagonal strips).
+__device__ __forceinline__ int block_of(const Item &it, int b) { return b < it.w ? it.cb0 + b : it.rb; }
 
 // Channel-major order: all strips of one channel are consecutive item indices.
 __device__ __forceinline__ Item decode_item(const Params &p, int g) {
@@ -122,16 +125,9 @@ __device__ __forceinline__ Item decode_item(const Params &p, int g) {
     it.job = j;
     it.f = l / jb.strips;
     decode_strip(l % jb.strips, jb.nb, p.max_strip, it.rb, it.cb0, it.w);
-    it.nblk = it.w;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) it.blk[c] = it.cb0 + c;
-    if (it.rb < it.cb0) {
-        it.blk[min(it.nblk, 3)] = it.rb;
-        it.a_slot = it.nblk;
-        ++it.nblk;
-    } else {
-        it.a_slot = 0;
-    }
+    const bool off_diag = it.rb < it.cb0;
+    it.nblk = it.w + (off_diag ? 1 : 0);
+    it.a_slot = off_diag ? it.w : 0;
     return it;
 }
 
@@ -173,7 +169,8 @@ __global__ void __launch_bounds__(256) unpack_k_kernel(const uint8_t *__restrict
     }
 }
 
-// MN-major: Y[f][t][0..R) = codes (16 Re x_0, Im x_0, 16 Re x_1, ...), zero past 2N and past T.
+// MN-major: Y[f][t][0..R) = E5M2 codes in groups of four inputs (16 Re x_0..16 Re x_3, Im x_0..
+// Im x_3, 16 Re x_4, ...), zero past 2N and past T.
 // One thread per 32 output bytes (16 samples in): grid-stride over F * ldy * (R / 32).
 __global__ void __launch_bounds__(256) unpack_mn_kernel(const uint8_t *__restrict__ frame, uint8_t *__restrict__ y,
                                                         int N, int F, int T, int R, int64_t ldy) {
@@ -198,65 +195,84 @@ __global__ void __launch_bounds__(256) unpack_mn_kernel(const uint8_t *__restric
 
 // ----------------------------------------------------------------------------- epilogue
 
-// Drains 32 TMEM columns (16 column pairs j) of this thread's lane (one row of G) and writes the
-// 8 complex visibilities this thread owns: even lanes (row 2i) take the first 8 j, odd lanes
-// (row 2i+1) the last 8; each obtains the other row's two values per j from its lane partner.
-// kScaled: the operand carries 16*Re, so G[re,re] = 256 x, G[re,im] = G[im,re] = 16 x.
-template <bool kScaled>
-__device__ __forceinline__ void drain_chunk(uint32_t taddr, int32_t *__restrict__ vis_f, int N, int i, bool odd,
-                                            int j0, bool add) {
+// Row (and column) order of the operand blocks. K-major engine: interleaved pairs, row 2n = Re x_n,
+// row 2n+1 = Im x_n. MN-major engines: groups of four inputs, rows 8g..8g+3 = 16 Re x_{4g..4g+3},
+// rows 8g+4..8g+7 = Im x_{4g..4g+3} (the order the byte expansion produces cheaply).
+template <bool kMN>
+struct Order {
+    static __device__ __forceinline__ int input_of(int m) { return kMN ? 4 * (m >> 3) + (m & 3) : m >> 1; }
+    static __device__ __forceinline__ int comp_of(int m) { return kMN ? (m >> 2) & 1 : m & 1; }
+    static constexpr int kPartner = kMN ? 4 : 1;   // lane holding the other component of the same input
+    // register (column within a 32-column chunk) of local output column jj (0..15), component c
+    static __host__ __device__ constexpr int reg(int jj, int c) { return kMN ? 8 * (jj >> 2) + (jj & 3) + 4 * c : 2 * jj + c; }
+};
+
+// One 32-column chunk of this thread's TMEM lane (one row of G, 16 output columns j0..j0+15):
+// FP32 -> int32 (removing the operand scale 16 of Re), then the 2x2 Re/Im combine with the lane
+// holding the other component of input i. The Re-row lane produces j0..j0+7, the Im-row lane
+// j0+8..j0+15: V = (G[re,re] + G[im,im]) + i (G[im,re] - G[re,im]).
+template <bool kMN>
+__device__ __forceinline__ void combine_chunk(uint32_t taddr, bool im_row, int (&vr)[8], int (&vi)[8]) {
+    using O = Order<kMN>;
     uint32_t r[32];
     dev::tmem_ld_32x32b_x32(taddr, r);
     dev::tmem_ld_wait();
     int g[32];
-    const float s_even = kScaled ? (odd ? 1.0f / 16.0f : 1.0f / 256.0f) : 1.0f;   // column 2j (re)
-    const float s_odd = kScaled ? (odd ? 1.0f : 1.0f / 16.0f) : 1.0f;             // column 2j+1 (im)
+    // scales: G[re,re] = 256 x, G[re,im] = G[im,re] = 16 x, G[im,im] = x (MN engines only)
+    const float s_re_col = kMN ? (im_row ? 1.0f / 16.0f : 1.0f / 256.0f) : 1.0f;
+    const float s_im_col = kMN ? (im_row ? 1.0f : 1.0f / 16.0f) : 1.0f;
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        g[2 * k] = __float2int_rn(__uint_as_float(r[2 * k]) * s_even);
-        g[2 * k + 1] = __float2int_rn(__uint_as_float(r[2 * k + 1]) * s_odd);
+    for (int jj = 0; jj < 16; ++jj) {
+        g[O::reg(jj, 0)] = __float2int_rn(__uint_as_float(r[O::reg(jj, 0)]) * s_re_col);
+        g[O::reg(jj, 1)] = __float2int_rn(__uint_as_float(r[O::reg(jj, 1)]) * s_im_col);
     }
-    int vr[8], vi[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int s0 = odd ? g[2 * k] : g[16 + 2 * k];
-        const int s1 = odd ? g[2 * k + 1] : g[16 + 2 * k + 1];
-        const int r0 = __shfl_xor_sync(0xffffffffu, s0, 1);
-        const int r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
-        if (!odd) {   // j = j0 + k: G[2i,2j] = g[2k], G[2i,2j+1] = g[2k+1]; partner row 2i+1: r0, r1
-            vr[k] = g[2 * k] + r1;
-            vi[k] = r0 - g[2 * k + 1];
-        } else {      // j = j0 + 8 + k: G[2i+1,2j] = g[16+2k], G[2i+1,2j+1] = g[17+2k]; partner: r0, r1
-            vr[k] = r0 + g[16 + 2 * k + 1];
-            vi[k] = g[16 + 2 * k] - r1;
+        const int s0 = im_row ? g[O::reg(k, 0)] : g[O::reg(8 + k, 0)];
+        const int s1 = im_row ? g[O::reg(k, 1)] : g[O::reg(8 + k, 1)];
+        const int r0 = __shfl_xor_sync(0xffffffffu, s0, O::kPartner);
+        const int r1 = __shfl_xor_sync(0xffffffffu, s1, O::kPartner);
+        if (!im_row) {   // j = j0 + k: own G[re_i,re_j], G[re_i,im_j]; partner G[im_i,re_j], G[im_i,im_j]
+            vr[k] = g[O::reg(k, 0)] + r1;
+            vi[k] = r0 - g[O::reg(k, 1)];
+        } else {         // j = j0 + 8 + k: own G[im_i,re_j], G[im_i,im_j]; partner G[re_i,re_j], G[re_i,im_j]
+            vr[k] = r0 + g[O::reg(8 + k, 1)];
+            vi[k] = g[O::reg(8 + k, 0)] - r1;
         }
     }
-    if (i >= N) return;
-    const int jb = j0 + (odd ? 8 : 0);
-    const int64_t prow = (int64_t)i * N - (int64_t)i * (i - 1) / 2 - i;   // p(i, j) = prow + j
+}
+
+// Visibilities j = jb .. jb+7 of row i live at vis_f[2 (prow + j)]: valid for i <= j < N.
+__device__ __forceinline__ void load_old(const int32_t *vis_f, int64_t prow, int i, int jb, int N, bool i_ok,
+                                         int2 (&old)[8]) {
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int j = jb + k;
-        if (j >= i && j < N) {
-            int2 *dst = reinterpret_cast<int2 *>(vis_f + 2 * (prow + j));
-            int2 v = make_int2(vr[k], vi[k]);
-            if (add) {
-                const int2 o = *dst;
-                v.x += o.x;
-                v.y += o.y;
-            }
-            *dst = v;
-        }
+        old[k] = (i_ok && j >= i && j < N) ? *reinterpret_cast<const int2 *>(vis_f + 2 * (prow + j)) : make_int2(0, 0);
+    }
+}
+
+__device__ __forceinline__ void store_vis(int32_t *vis_f, int64_t prow, int i, int jb, int N, bool i_ok,
+                                          const int (&vr)[8], const int (&vi)[8], const int2 (&old)[8]) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int j = jb + k;
+        if (i_ok && j >= i && j < N)
+            *reinterpret_cast<int2 *>(vis_f + 2 * (prow + j)) = make_int2(vr[k] + old[k].x, vi[k] + old[k].y);
     }
 }
 
 // ----------------------------------------------------------------------------- GEMM kernel
 
+constexpr int kEpiWarps = 8;                  // two per TMEM lane quarter
+constexpr int kEpiWarp0 = 2;
+constexpr int kConvWarp0 = kEpiWarp0 + kEpiWarps;
+
 template <int kEngine>
 struct Cfg {
     static constexpr bool kFused = kEngine == kFusedMN;
     static constexpr bool kMN = kEngine != kUnpackedK;
-    static constexpr int kThreads = kFused ? 192 + 32 * kConvWarps : 192;
+    static constexpr int kThreads = 32 * (kConvWarp0 + (kFused ? kConvWarps : 0));
 };
 
 template <int kEngine>
@@ -285,7 +301,7 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t op_base = dev::smem_u32(op_ring);
     const uint32_t pk_base = dev::smem_u32(pk_ring);
-    const int n_item_consumers = 1 + 4 + (C::kFused ? kConvWarps : 0);
+    const int n_item_consumers = 1 + kEpiWarps + (C::kFused ? kConvWarps : 0);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.op_stages; ++s) {
@@ -298,7 +314,7 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
         }
         for (int a = 0; a < 2; ++a) {
             dev::mbar_init(&acc_full[a], 1);
-            dev::mbar_init(&acc_empty[a], 4);
+            dev::mbar_init(&acc_empty[a], kEpiWarps);
         }
         for (int s = 0; s < kItemRing; ++s) {
             dev::mbar_init(&item_full[s], 1);
@@ -373,13 +389,13 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
                     for (int b = 0; b < it.nblk; ++b) {
                         if (C::kFused)
                             dev::tma_load_3d(pk_base + s * pk_stage_bytes + b * kPkSlotBytes, &jb.tmap, &full[s],
-                                             it.blk[b] * 64, it.f, kt * kKt);
+                                             block_of(it, b) * 64, it.f, kt * kKt);
                         else if (C::kMN)
                             dev::tma_load_3d(op_base + s * op_stage_bytes + b * kOpSlotBytes, &jb.tmap, &full[s],
-                                             it.blk[b] * kBlk, kt * kKt, it.f);
+                                             block_of(it, b) * kBlk, kt * kKt, it.f);
                         else
                             dev::tma_load_3d(op_base + s * op_stage_bytes + b * kOpSlotBytes, &jb.tmap, &full[s],
-                                             kt * kKt, it.blk[b] * kBlk, it.f);
+                                             kt * kKt, block_of(it, b) * kBlk, it.f);
                     }
                     issued |= 1u << s;
                     issued_parity = (issued_parity & ~(1u << s)) | (ph << s);
@@ -393,7 +409,7 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
         if (lane == 0) {
             // ---------------------------------------------------------------- MMA issuer
             uint32_t s = 0, ph = 0;
-            uint32_t acc = 0, acc_ph[2] = {0, 0};
+            uint32_t acc = 0, acc_ph = 0;            // bit a: phase parity of accumulator a
             bool ok = true;
             while (ok) {
                 const int g = next_item(false);
@@ -402,7 +418,7 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
                 const Job &jb = p.jobs[it.job];
                 for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles) {
                     const int k1 = min(jb.k_tiles, k0 + p.k_flush_tiles);
-                    if (!wait(&acc_empty[acc], acc_ph[acc] ^ 1)) { ok = false; break; }
+                    if (!wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u)) { ok = false; break; }
                     dev::tc_fence_after();
                     const uint32_t d0 = tmem + acc * 256u;
                     for (int kt = k0; kt < k1; ++kt) {
@@ -433,19 +449,24 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
                     }
                     if (!ok) break;
                     dev::tc_commit(&acc_full[acc]);
-                    acc_ph[acc] ^= 1;
-                    acc = (acc + 1) % p.n_acc;
+                    acc_ph ^= 1u << acc;
+                    acc = (acc + 1 == (uint32_t)p.n_acc) ? 0u : acc + 1;
                 }
             }
             dev::tc_commit(done);
             dev::mbar_wait(done, 0, p.limit_ns);
         }
-    } else if (warp < 6) {
+    } else if (warp < kConvWarp0) {
         // -------------------------------------------------------------------- epilogue warps
-        const int q = warp & 3;                 // TMEM lane quarter this warp may access
+        // Warp w reads TMEM lane quarter w % 4; the two warps of a quarter split the 32-column
+        // chunks of an item between them. The accumulate-mode loads of the next chunk are issued
+        // before the current chunk is combined, so their latency overlaps useful work.
+        using O = Order<C::kMN>;
+        const int q = warp & 3;
+        const int half = (warp - kEpiWarp0) >> 2;
         const int m = q * 32 + lane;            // row of the 128-row tile
-        const bool odd = (m & 1) != 0;
-        uint32_t acc = 0, acc_ph[2] = {0, 0};
+        const bool im_row = O::comp_of(m) != 0;
+        uint32_t acc = 0, acc_ph = 0;
         bool ok = true;
         while (ok) {
             const int g = next_item(true);
@@ -453,32 +474,60 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
             const Item it = decode_item(p, g);
             const Job &jb = p.jobs[it.job];
             const int N = jb.n_inputs;
-            const int i = (it.rb * kBlk + m) >> 1;
+            const int i = it.rb * (kBlk / 2) + O::input_of(m);
+            const bool i_ok = i < N;
+            const int64_t prow = (int64_t)i * N - (int64_t)i * (i - 1) / 2 - i;   // p(i, j) = prow + j
             int32_t *vis_f = jb.vis + (size_t)it.f * (size_t)npairs(N) * 2;
+            const int n_chunks = it.w * (kBlk / 32);
             for (int k0 = 0; k0 < jb.k_tiles; k0 += p.k_flush_tiles) {
-                if (!wait(&acc_full[acc], acc_ph[acc])) { ok = false; break; }
+                if (!wait(&acc_full[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
                 dev::tc_fence_after();
                 const bool add = jb.accumulate || k0 > 0;
                 const uint32_t tb = tmem + acc * 256u + (uint32_t(q * 32) << 16);
-                for (int c = 0; c < it.w; ++c)
+                auto jb_of = [&](int ck) {           // first output column of chunk ck for this lane
+                    return (it.cb0 * kBlk + ck * 32) / 2 + (im_row ? 8 : 0);
+                };
+                int2 old[8], nxt[8];
+                int ck = half;
+                if (add && ck < n_chunks) load_old(vis_f, prow, i, jb_of(ck), N, i_ok, old);
+                else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) old[k] = make_int2(0, 0);
+                }
 #pragma unroll 1
-                    for (int ch = 0; ch < kBlk / 32; ++ch)
-                        drain_chunk<C::kMN>(tb + c * kBlk + ch * 32, vis_f, N, i, odd,
-                                            ((it.cb0 + c) * kBlk + ch * 32) >> 1, add);
+                for (; ck < n_chunks; ck += 2) {
+                    const bool more = ck + 2 < n_chunks;
+                    if (add && more) load_old(vis_f, prow, i, jb_of(ck + 2), N, i_ok, nxt);
+                    int vr[8], vi[8];
+                    combine_chunk<C::kMN>(tb + ck * 32, im_row, vr, vi);
+                    store_vis(vis_f, prow, i, jb_of(ck), N, i_ok, vr, vi, old);
+                    if (add && more) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) old[k] = nxt[k];
+                    }
+                }
                 dev::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) dev::mbar_arrive(&acc_empty[acc]);
-                acc_ph[acc] ^= 1;
-                acc = (acc + 1) % p.n_acc;
+                acc_ph ^= 1u << acc;
+                acc = (acc + 1 == (uint32_t)p.n_acc) ? 0u : acc + 1;
             }
         }
     } else if (C::kFused) {
         // -------------------------------------------------------------------- converter warps
         // Packed tile [128 t][pw bytes] -> MN-major operand rows: row t of block b holds the 128
-        // codes (16 Re, Im) of inputs 64*blk .. 64*blk+63 at sample t, 16-byte chunks swizzled
-        // as chunk ^ (t & 7) (the 128-byte swizzle the MMA descriptor names).
-        const int ctid = threadIdx.x - 192;
+        // codes of inputs 64*blk .. 64*blk+63 at sample t in the grouped order, 16-byte chunks
+        // swizzled as chunk ^ (t & 7) (the 128-byte swizzle the MMA descriptor names).
+        // Each thread owns two fixed (t, 16-byte chunk) positions of every block.
+        const int ctid = threadIdx.x - 32 * kConvWarp0;
         uint32_t ps = 0, pph = 0, os = 0, oph = 0;
+        uint32_t dst0[2], dst1[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int r = ctid + 256 * u, t = r >> 2, c = r & 3;
+            dst0[u] = t * 128 + (((2 * c) ^ (t & 7)) << 4);
+            dst1[u] = t * 128 + (((2 * c + 1) ^ (t & 7)) << 4);
+        }
         bool ok = true;
         while (ok) {
             const int g = next_item(true);
@@ -486,28 +535,39 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
             const Item it = decode_item(p, g);
             const Job &jb = p.jobs[it.job];
             const int pw = jb.pw;
+            uint32_t src[2];
+            bool have[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int r = ctid + 256 * u, t = r >> 2, c = r & 3;
+                src[u] = t * pw + 16 * c;
+                have[u] = 16 * c < pw;
+            }
             for (int kt = 0; kt < jb.k_tiles; ++kt) {
                 if (!wait(&pk_full[ps], pph)) { ok = false; break; }
                 if (!wait(&op_empty[os], oph ^ 1)) { ok = false; break; }
                 const uint32_t pk = pk_base + ps * pk_stage_bytes;
                 const uint32_t op = op_base + os * op_stage_bytes;
-                for (int task = ctid; task < it.nblk * 512; task += 32 * kConvWarps) {
-                    const int b = task >> 9, r = task & 511;
-                    const int t = r >> 2, c = r & 3;
-                    uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-                    if (c * 16 < pw) {
-                        uint4 v;
-                        asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
-                                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                                     : "r"(pk + b * kPkSlotBytes + t * pw + c * 16));
-                        dev::expand16_e5m2(v, lo, hi);
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    if (b < it.nblk) {
+#pragma unroll
+                        for (int u = 0; u < 2; ++u) {
+                            uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+                            if (have[u]) {
+                                uint4 v;
+                                asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                                             : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                                             : "r"(pk + b * kPkSlotBytes + src[u]));
+                                dev::expand16_e5m2(v, lo, hi);
+                            }
+                            const uint32_t row = op + b * kOpSlotBytes;
+                            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                                         ::"r"(row + dst0[u]), "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w));
+                            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                                         ::"r"(row + dst1[u]), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
+                        }
                     }
-                    const uint32_t row = op + b * kOpSlotBytes + t * 128;
-                    const uint32_t sw = t & 7;
-                    asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
-                                 ::"r"(row + (((2 * c) ^ sw) << 4)), "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w));
-                    asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
-                                 ::"r"(row + (((2 * c + 1) ^ sw) << 4)), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
                 }
                 dev::fence_proxy_async_smem();
                 __syncwarp();

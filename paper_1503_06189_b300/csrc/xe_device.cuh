@@ -199,13 +199,15 @@ __device__ __forceinline__ uint32_t nibbles_to_e5m2(uint32_t lo_nibbles) {
     return __byte_perm(d01, d23, 0x7531);
 }
 
-// Four packed samples (bytes re<<4 | im, 4-bit two's complement) -> eight E5M2 codes in sample
-// order, each sample as (16*re, im). Per half-precision lane: (x & 0x000F) ^ 0x6408 has the bits of
-// 1024 + (im ^ 8) = 1032 + im, and (x & 0x00F0) ^ 0x6480 those of 1024 + 16*(re ^ 8) = 1152 + 16*re;
-// subtracting 1032 resp. 1152 is exact and leaves im resp. 16*re, whose low bytes are zero, so
-// the high bytes are their E5M2 codes. 13 integer/half2 operations for 8 codes.
-__device__ __forceinline__ void expand4_e5m2(uint32_t x, uint32_t &w0, uint32_t &w1) {
-    const uint32_t x8 = x >> 8;
+// Four packed samples x_0..x_3 (bytes re<<4 | im, 4-bit two's complement) -> eight E5M2 codes,
+// returned as wre = (16 re_0, 16 re_1, 16 re_2, 16 re_3) and wim = (im_0, .., im_3). Per
+// half-precision lane, (x & 0x000F) ^ 0x6408 has the bits of 1024 + (im ^ 8) = 1032 + im and
+// (x & 0x00F0) ^ 0x6480 those of 1024 + 16 (re ^ 8) = 1152 + 16 re; subtracting 1032 resp. 1152 is
+// exact and leaves im resp. 16 re, whose low bytes are zero, so their high bytes are the E5M2 codes.
+// Six logic/permute operations (the ALU pipe), one integer multiply-high (x >> 8, on the FMA pipe)
+// and four half2 subtractions for eight codes.
+__device__ __forceinline__ void expand4_e5m2(uint32_t x, uint32_t &wre, uint32_t &wim) {
+    const uint32_t x8 = __umulhi(x, 1u << 24);
     uint32_t im02 = (x & 0x000F000Fu) ^ 0x64086408u;
     uint32_t im13 = (x8 & 0x000F000Fu) ^ 0x64086408u;
     uint32_t re02 = (x & 0x00F000F0u) ^ 0x64806480u;
@@ -215,12 +217,12 @@ __device__ __forceinline__ void expand4_e5m2(uint32_t x, uint32_t &w0, uint32_t 
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(im13) : "r"(k_im));
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re02) : "r"(k_re));
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re13) : "r"(k_re));
-    const uint32_t re = __byte_perm(re02, re13, 0x7351);   // re0 re1 re2 re3
-    const uint32_t im = __byte_perm(im02, im13, 0x7351);   // im0 im1 im2 im3
-    w0 = __byte_perm(re, im, 0x5140);                      // re0 im0 re1 im1
-    w1 = __byte_perm(re, im, 0x7362);                      // re2 im2 re3 im3
+    wre = __byte_perm(re02, re13, 0x7351);
+    wim = __byte_perm(im02, im13, 0x7351);
 }
 
+// 16 packed samples -> 32 E5M2 codes in groups of four inputs: (16 re_0..16 re_3, im_0..im_3,
+// 16 re_4.., im_4.., ...). This is the operand row order of the MN-major engines.
 __device__ __forceinline__ void expand16_e5m2(const uint4 &in, uint4 &lo, uint4 &hi) {
     expand4_e5m2(in.x, lo.x, lo.y);
     expand4_e5m2(in.y, lo.z, lo.w);

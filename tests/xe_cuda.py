@@ -35,8 +35,9 @@ def correlate_batched(frames, tune=None, accumulate=False):
 
 
 def e5m2_codes(frame):
-    """Expected unpack output [F][ldy][R] of a frame: per sample t, (16 Re, Im) E5M2 codes of every
-    input in order, zero padded. E5M2 codes taken from numpy's float16 (E5M2 = its high byte)."""
+    """Expected unpack output [F][ldy][R] of a frame: per sample t and group of four inputs, the
+    E5M2 codes of (16 Re x_4g..x_4g+3, Im x_4g..x_4g+3), zero padded. E5M2 codes taken from numpy's
+    float16 (E5M2 = its high byte)."""
     T, F, N = frame.shape
     b = frame.astype(np.int64)
     re = ((b >> 4) ^ 8) - 8
@@ -45,6 +46,8 @@ def e5m2_codes(frame):
     ldy = -(-max(T, 1) // 128) * 128
     out = np.zeros((F, ldy, R), np.uint8)
     code = lambda v: (v.astype(np.float16).view(np.uint16) >> 8).astype(np.uint8)
-    out[:, :T, 0:2 * N:2] = code(16 * re).transpose(1, 0, 2)
-    out[:, :T, 1:2 * N:2] = code(im).transpose(1, 0, 2)
+    n = np.arange(N)
+    row_re = 8 * (n // 4) + (n % 4)
+    out[:, :T, row_re] = code(16 * re).transpose(1, 0, 2)
+    out[:, :T, row_re + 4] = code(im).transpose(1, 0, 2)
     return out, R, ldy
