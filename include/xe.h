@@ -120,9 +120,10 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
 typedef struct {
     int32_t engine;      /* XE_ENGINE_* */
     int32_t max_strip;   /* 1..4: 128x128 tiles per work item along a row; <= 2 double-buffers
-                            the tensor-memory accumulator (default 2) */
+                            the tensor-memory accumulator (default 4) */
     int32_t k_flush;     /* time samples accumulated in TMEM before draining to int32; multiple
-                            of 128; 0 = default */
+                            of 128, at most 32768 (keeps every FP32 partial sum below 2^22,
+                            where it is exact); 0 = default (32768) */
     int32_t n_ctas;      /* persistent CTAs; 0 = one per SM */
 } xe_tune;
 

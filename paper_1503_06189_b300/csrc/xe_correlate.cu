@@ -37,13 +37,16 @@ namespace xe {
 namespace corr {
 
 constexpr int kBlk = 128;                    // rows per operand block = MMA M
-constexpr int kKt = 128;                     // time samples per pipeline stage
-constexpr int kOpSlotBytes = kBlk * kKt;     // 16 KiB: one operand block for one stage
-constexpr int kPkSlotBytes = 64 * kKt;       // 8 KiB: 64 inputs x 128 samples, packed
+constexpr int kKtMax = 128;                  // time samples per pipeline stage (K-major engine)
+constexpr int kKtMN = 128;                   // time samples per pipeline stage (MN-major engines)
 constexpr int kTmemCols = 512;
 constexpr int kItemRing = 4;
 constexpr int kSmemMax = 232448;             // 227 KiB opt-in limit per block
-constexpr int kDefaultKFlush = 1 << 17;      // samples; 64 * 2^17 = 2^23 < 2^24
+// TMEM drain interval: with at most 2^15 samples per drain every accumulated value, and every sum
+// the epilogue forms from two of them, stays below 2^22 in magnitude (after the operand scales are
+// removed), so FP32 holds them exactly and the 1.5 * 2^23 rounding trick converts them to int32.
+constexpr int kDefaultKFlush = 1 << 15;
+constexpr int kMaxKFlush = 1 << 15;
 constexpr int kConvWarps = 8;
 
 enum Engine { kUnpackedK = 0, kUnpackedMN = 1, kFusedMN = 2 };
@@ -208,37 +211,37 @@ struct Order {
 };
 
 // One 32-column chunk of this thread's TMEM lane (one row of G, 16 output columns j0..j0+15):
-// FP32 -> int32 (removing the operand scale 16 of Re), then the 2x2 Re/Im combine with the lane
-// holding the other component of input i. The Re-row lane produces j0..j0+7, the Im-row lane
-// j0+8..j0+15: V = (G[re,re] + G[im,im]) + i (G[im,re] - G[re,im]).
+// the 2x2 Re/Im combine with the lane holding the other component of input i, in FP32 (exact: the
+// operands are integers times powers of two below 2^22), then to int32 by adding 1.5 * 2^23 and
+// subtracting its bit pattern. The Re-row lane produces j0..j0+7, the Im-row lane j0+8..j0+15:
+// V = (G[re,re] + G[im,im]) + i (G[im,re] - G[re,im]). MN engines: G[re,re] carries 256, G[re,im]
+// and G[im,re] 16, G[im,im] 1 (the operand holds 16 Re).
 template <bool kMN>
 __device__ __forceinline__ void combine_chunk(uint32_t taddr, bool im_row, int (&vr)[8], int (&vi)[8]) {
     using O = Order<kMN>;
     uint32_t r[32];
     dev::tmem_ld_32x32b_x32(taddr, r);
     dev::tmem_ld_wait();
-    int g[32];
-    // scales: G[re,re] = 256 x, G[re,im] = G[im,re] = 16 x, G[im,im] = x (MN engines only)
-    const float s_re_col = kMN ? (im_row ? 1.0f / 16.0f : 1.0f / 256.0f) : 1.0f;
-    const float s_im_col = kMN ? (im_row ? 1.0f : 1.0f / 16.0f) : 1.0f;
-#pragma unroll
-    for (int jj = 0; jj < 16; ++jj) {
-        g[O::reg(jj, 0)] = __float2int_rn(__uint_as_float(r[O::reg(jj, 0)]) * s_re_col);
-        g[O::reg(jj, 1)] = __float2int_rn(__uint_as_float(r[O::reg(jj, 1)]) * s_im_col);
-    }
+    constexpr float kRR = kMN ? 1.0f / 256.0f : 1.0f;   // scale of G[re,re]
+    constexpr float kRI = kMN ? 1.0f / 16.0f : 1.0f;    // scale of G[re,im] and G[im,re]
+    constexpr float kMagic = 12582912.0f;               // 1.5 * 2^23
+    constexpr int kMagicBits = 0x4B400000;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int s0 = im_row ? g[O::reg(k, 0)] : g[O::reg(8 + k, 0)];
-        const int s1 = im_row ? g[O::reg(k, 1)] : g[O::reg(8 + k, 1)];
-        const int r0 = __shfl_xor_sync(0xffffffffu, s0, O::kPartner);
-        const int r1 = __shfl_xor_sync(0xffffffffu, s1, O::kPartner);
+        const uint32_t s0 = im_row ? r[O::reg(k, 0)] : r[O::reg(8 + k, 0)];
+        const uint32_t s1 = im_row ? r[O::reg(k, 1)] : r[O::reg(8 + k, 1)];
+        const float r0 = __uint_as_float(__shfl_xor_sync(0xffffffffu, s0, O::kPartner));
+        const float r1 = __uint_as_float(__shfl_xor_sync(0xffffffffu, s1, O::kPartner));
+        float re, im;
         if (!im_row) {   // j = j0 + k: own G[re_i,re_j], G[re_i,im_j]; partner G[im_i,re_j], G[im_i,im_j]
-            vr[k] = g[O::reg(k, 0)] + r1;
-            vi[k] = r0 - g[O::reg(k, 1)];
+            re = fmaf(__uint_as_float(r[O::reg(k, 0)]), kRR, r1);
+            im = (r0 - __uint_as_float(r[O::reg(k, 1)])) * kRI;
         } else {         // j = j0 + 8 + k: own G[im_i,re_j], G[im_i,im_j]; partner G[re_i,re_j], G[re_i,im_j]
-            vr[k] = r0 + g[O::reg(8 + k, 1)];
-            vi[k] = g[O::reg(8 + k, 0)] - r1;
+            re = fmaf(r0, kRR, __uint_as_float(r[O::reg(8 + k, 1)]));
+            im = (__uint_as_float(r[O::reg(8 + k, 0)]) - r1) * kRI;
         }
+        vr[k] = __float_as_int(re + kMagic) - kMagicBits;
+        vi[k] = __float_as_int(im + kMagic) - kMagicBits;
     }
 }
 
@@ -273,11 +276,19 @@ struct Cfg {
     static constexpr bool kFused = kEngine == kFusedMN;
     static constexpr bool kMN = kEngine != kUnpackedK;
     static constexpr int kThreads = 32 * (kConvWarp0 + (kFused ? kConvWarps : 0));
+    static constexpr int kKt = kMN ? kKtMN : kKtMax;    // samples per stage
+    static constexpr int kOpSlotBytes = kBlk * kKt;     // one operand block for one stage
+    static constexpr int kPkSlotBytes = 64 * kKt;       // 64 inputs x kKt samples, packed
 };
+
+__host__ __device__ constexpr int kt_of(int engine) { return engine == kUnpackedK ? kKtMax : kKtMN; }
 
 template <int kEngine>
 __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(const __grid_constant__ Params p) {
     using C = Cfg<kEngine>;
+    constexpr int kKt = C::kKt;
+    constexpr int kOpSlotBytes = C::kOpSlotBytes;
+    constexpr int kPkSlotBytes = C::kPkSlotBytes;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int op_stage_bytes = p.slots * kOpSlotBytes;
@@ -513,35 +524,37 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
                 acc = (acc + 1 == (uint32_t)p.n_acc) ? 0u : acc + 1;
             }
         }
-    } else if (C::kFused) {
+    } else if constexpr (C::kFused) {
         // -------------------------------------------------------------------- converter warps
         // Packed tile [128 t][pw bytes] -> MN-major operand rows: row t of block b holds the 128
         // codes of inputs 64*blk .. 64*blk+63 at sample t in the grouped order, 16-byte chunks
         // swizzled as chunk ^ (t & 7) (the 128-byte swizzle the MMA descriptor names).
-        // Each thread owns two fixed (t, 16-byte chunk) positions of every block.
+        // Each thread owns kTasks fixed (t, 16-byte chunk) positions of every block: kKt samples x
+        // 4 chunks per block, spread over the 256 converter threads.
+        constexpr int kTasks = kKt * 4 / (32 * kConvWarps);
+        static_assert(kTasks * 32 * kConvWarps == kKt * 4, "conversion tasks divide evenly");
         const int ctid = threadIdx.x - 32 * kConvWarp0;
-        uint32_t ps = 0, pph = 0, os = 0, oph = 0;
-        uint32_t dst0[2], dst1[2];
+        uint32_t dst0[kTasks], dst1[kTasks];
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const int r = ctid + 256 * u, t = r >> 2, c = r & 3;
+        for (int u = 0; u < kTasks; ++u) {
+            const int r = ctid + 32 * kConvWarps * u, t = r >> 2, c = r & 3;
             dst0[u] = t * 128 + (((2 * c) ^ (t & 7)) << 4);
             dst1[u] = t * 128 + (((2 * c + 1) ^ (t & 7)) << 4);
         }
+        uint32_t ps = 0, pph = 0, os = 0, oph = 0;
         bool ok = true;
         while (ok) {
             const int g = next_item(true);
             if (g < 0) break;
             const Item it = decode_item(p, g);
             const Job &jb = p.jobs[it.job];
-            const int pw = jb.pw;
-            uint32_t src[2];
-            bool have[2];
+            uint32_t src[kTasks];
+            bool have[kTasks];
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int r = ctid + 256 * u, t = r >> 2, c = r & 3;
-                src[u] = t * pw + 16 * c;
-                have[u] = 16 * c < pw;
+            for (int u = 0; u < kTasks; ++u) {
+                const int r = ctid + 32 * kConvWarps * u, t = r >> 2, c = r & 3;
+                src[u] = t * jb.pw + 16 * c;
+                have[u] = 16 * c < jb.pw;
             }
             for (int kt = 0; kt < jb.k_tiles; ++kt) {
                 if (!wait(&pk_full[ps], pph)) { ok = false; break; }
@@ -552,7 +565,7 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
                 for (int b = 0; b < 4; ++b) {
                     if (b < it.nblk) {
 #pragma unroll
-                        for (int u = 0; u < 2; ++u) {
+                        for (int u = 0; u < kTasks; ++u) {
                             uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
                             if (have[u]) {
                                 uint4 v;
@@ -597,10 +610,11 @@ struct JobGeom {
 
 static JobGeom geom(const xe_shape &s, int engine) {
     JobGeom g;
+    const int kt = kt_of(engine);
     g.R = (int)round_up(2 * (int64_t)s.n_inputs, kBlk);
     g.nb = g.R / kBlk;
-    g.ldy = round_up(std::max<int64_t>(s.n_time, 1), kKt);
-    g.k_tiles = (int)((s.n_time + kKt - 1) / kKt);
+    g.ldy = round_up(std::max<int64_t>(s.n_time, 1), kKtMax);
+    g.k_tiles = (int)((s.n_time + kt - 1) / kt);
     g.y_bytes = engine == kFusedMN ? 0 : (size_t)round_up((int64_t)s.n_chan * g.R * g.ldy, 1024);
     return g;
 }
@@ -623,7 +637,7 @@ static int engine_of(int api_engine) {
 
 static void resolve_tune(const xe_tune *t, xe_tune &out) {
     out.engine = XE_ENGINE_FUSED;
-    out.max_strip = 2;
+    out.max_strip = 4;
     out.k_flush = kDefaultKFlush;
     out.n_ctas = 0;
     if (!t) return;
@@ -636,7 +650,7 @@ static void resolve_tune(const xe_tune *t, xe_tune &out) {
 static int check_tune(const xe_tune &t) {
     if (engine_of(t.engine) < 0) return XE_EINVAL;
     if (t.max_strip < 1 || t.max_strip > 4) return XE_EINVAL;
-    if (t.k_flush < kKt || t.k_flush % kKt || t.k_flush > (1 << 18)) return XE_EINVAL;
+    if (t.k_flush < kKtMax || t.k_flush % kKtMax || t.k_flush > kMaxKFlush) return XE_EINVAL;
     if (t.n_ctas < 0) return XE_EINVAL;
     return XE_OK;
 }
@@ -719,19 +733,20 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             const uint32_t pw = (uint32_t)std::min(64, s.n_inputs);
             const uint64_t dims[3] = {(uint64_t)s.n_inputs, (uint64_t)s.n_chan, (uint64_t)s.n_time};
             const uint64_t strides[2] = {(uint64_t)s.n_inputs, (uint64_t)s.n_inputs * s.n_chan};
-            const uint32_t box[3] = {pw, 1, kKt};
+            const uint32_t box[3] = {pw, 1, (uint32_t)kKtMN};
             enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(jobs[j].frame), dims,
                                strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
             d.pw = (int)pw;
         } else {
             if (int e = launch_unpack(engine, jobs[j].frame, s, y, g.ldy, st)) return e;
-            const uint32_t box[3] = {kKt, kBlk, 1};
             if (engine == kUnpackedMN) {
+                const uint32_t box[3] = {kBlk, (uint32_t)kKtMN, 1};
                 const uint64_t dims[3] = {(uint64_t)g.R, (uint64_t)g.ldy, (uint64_t)s.n_chan};
                 const uint64_t strides[2] = {(uint64_t)g.R, (uint64_t)g.R * g.ldy};
                 enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, y, dims, strides, box,
                                    CU_TENSOR_MAP_SWIZZLE_128B);
             } else {
+                const uint32_t box[3] = {(uint32_t)kKtMax, kBlk, 1};
                 const uint64_t dims[3] = {(uint64_t)g.ldy, (uint64_t)g.R, (uint64_t)s.n_chan};
                 const uint64_t strides[2] = {(uint64_t)g.ldy, (uint64_t)g.ldy * g.R};
                 enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, y, dims, strides, box,
@@ -757,7 +772,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     hp.n_jobs = nj;
     hp.n_items = items;
     hp.max_strip = tune.max_strip;
-    hp.k_flush_tiles = tune.k_flush / kKt;
+    hp.k_flush_tiles = tune.k_flush / kt_of(engine);
     hp.slots = tune.max_strip == 1 ? 2 : (tune.max_strip == 2 ? 3 : 4);
     hp.n_acc = tune.max_strip <= 2 ? 2 : 1;
     hp.status = status;
@@ -765,15 +780,16 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     hp.limit_ns = wait_limit_ns();
     const int bar_bytes = 1024;
     const int avail = kSmemMax - 1024 - bar_bytes;
+    const int op_slot = kBlk * kt_of(engine), pk_slot = 64 * kt_of(engine);
     if (engine == kFusedMN) {
         hp.pk_stages = 3;
-        hp.op_stages = std::min(4, (avail - hp.pk_stages * hp.slots * kPkSlotBytes) / (hp.slots * kOpSlotBytes));
+        hp.op_stages = std::min(8, (avail - hp.pk_stages * hp.slots * pk_slot) / (hp.slots * op_slot));
     } else {
         hp.pk_stages = 0;
-        hp.op_stages = std::min(6, avail / (hp.slots * kOpSlotBytes));
+        hp.op_stages = std::min(8, avail / (hp.slots * op_slot));
     }
     if (hp.op_stages < 2) return XE_EINVAL;
-    const int smem = 1024 + hp.op_stages * hp.slots * kOpSlotBytes + hp.pk_stages * hp.slots * kPkSlotBytes + bar_bytes;
+    const int smem = 1024 + hp.op_stages * hp.slots * op_slot + hp.pk_stages * hp.slots * pk_slot + bar_bytes;
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     XE_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
     switch (engine) {
