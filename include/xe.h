@@ -96,6 +96,28 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
                 int32_t groups_per_stream, xe_shape s, uint8_t *frame, uint8_t *filled,
                 uint32_t *lost, uint32_t *stats, void *ws, size_t ws_bytes, void *stream);
 
+/*
+ * Allocation-free variant of xe_assemble. The paper has no counterpart to this call: it exists for
+ * callers that cannot allocate device memory where they assemble frames -- for example code that
+ * runs while a stream is being captured into a CUDA graph (cudaMalloc is not a stream operation
+ * and cannot be captured), real-time receive loops that must not block (cudaMalloc can synchronise
+ * the device and stall for milliseconds), or plug-ins whose host application owns every device
+ * allocation and hands out no scratch space.
+ *
+ * Arguments and results are those of xe_assemble, without the workspace: the owner table lives in
+ * a static array inside libxe of XE_ASSEMBLE_NOALLOC_MAX_SLOTS entries (1 MiB per device that loads
+ * the library, held until the process exits). A frame may use at most that many (slot, group)
+ * pairs, (T/4) * (F/8) <= XE_ASSEMBLE_NOALLOC_MAX_SLOTS; larger frames return XE_ENOMEM.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture. The call allocates nothing. All calls share the one array
+ * and each call resets the part it uses, so calls whose kernels may overlap on the GPU (different
+ * streams, or overlapping graph nodes) race and must be serialised by the caller.
+ */
+#define XE_ASSEMBLE_NOALLOC_MAX_SLOTS (1 << 18)
+int xe_assemble_noalloc(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
+                        int32_t groups_per_stream, xe_shape s, uint8_t *frame, uint8_t *filled,
+                        uint32_t *lost, uint32_t *stats, void *stream);
+
 /* ---------------------------------------------------------------- A2: unpack */
 
 /*

@@ -23,7 +23,7 @@ XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K = 0, 1
 
 EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",
-    "xe_assemble_workspace_size", "xe_assemble", "xe_unpack", "xe_correlate_workspace_size",
+    "xe_assemble_workspace_size", "xe_assemble", "xe_assemble_noalloc", "xe_unpack", "xe_correlate_workspace_size",
     "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched", "xe_normalize",
 ]
 
@@ -71,6 +71,7 @@ def _load():
     L.xe_assemble_workspace_size.restype = sz
     L.xe_assemble_workspace_size.argtypes = [Shape]
     L.xe_assemble.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, vp, vp, vp, sz, vp]
+    L.xe_assemble_noalloc.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, vp, vp, vp]
     L.xe_unpack.argtypes = [vp, Shape, vp, i64, vp]
     L.xe_correlate_workspace_size.restype = sz
     L.xe_correlate_workspace_size.argtypes = [Shape]
@@ -170,6 +171,19 @@ def xe_assemble(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream
     _check(_L.xe_assemble(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(frame),
                             _ptr(filled), _ptr(lost), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)),
            "xe_assemble")
+
+
+XE_ASSEMBLE_NOALLOC_MAX_SLOTS = 1 << 18
+
+
+def xe_assemble_noalloc(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
+                        frame, filled, lost, stats, stream=None):
+    """xe_assemble without a workspace, for callers that cannot allocate device memory at this point
+    (stream capture, non-blocking real-time loops, hosts that own all device memory): the owner
+    table is a fixed 1 MiB array inside libxe shared by every call, so calls must not overlap on the
+    GPU, and frames with (T/4)*(F/8) above XE_ASSEMBLE_NOALLOC_MAX_SLOTS are rejected (XE_ENOMEM)."""
+    _check(_L.xe_assemble_noalloc(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(frame),
+                                  _ptr(filled), _ptr(lost), _ptr(stats), _stream(stream)), "xe_assemble_noalloc")
 
 
 # ----------------------------------------------------------------------------- A2..A4

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "xe_internal.h"
 
@@ -149,3 +150,75 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------- allocation-free variant
+// xe_assemble_noalloc runs the same three kernels as xe_assemble, but its owner table lives in a
+// fixed-size array compiled into the library instead of in caller-provided workspace. It exists
+// for callers that cannot obtain device memory at the point where they assemble frames (see the
+// declaration in xe.h). Every call on a device shares this one array.
+
+namespace xe {
+namespace asmb {
+
+static __device__ __align__(256) uint32_t g_noalloc_owner[XE_ASSEMBLE_NOALLOC_MAX_SLOTS];
+
+// Device address of g_noalloc_owner on the current device, resolved once per device. In host code
+// the symbol itself is only a host-side stand-in, so the kernels must be given this address.
+static uint32_t *noalloc_owner(int *status) {
+    static uint32_t *addr[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { *status = cuda_fail(e); return nullptr; }
+    if (dev < 0 || dev >= 64) { *status = XE_EINVAL; return nullptr; }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_owner);
+        if (e != cudaSuccess || !p) { *status = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol); return nullptr; }
+        addr[dev] = static_cast<uint32_t *>(p);
+    }
+    return addr[dev];
+}
+
+}  // namespace asmb
+}  // namespace xe
+
+extern "C" int xe_assemble_noalloc(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
+                                   int32_t gps, xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost,
+                                   uint32_t *stats, void *stream) {
+    if (!valid_shape(s) || s.n_time < 4 || s.n_time % 4 || s.n_chan % 8 || gps < 1 || (s.n_chan / 8) % gps)
+        return XE_EINVAL;
+    if (!frame || !filled || !lost || !stats || (n_pkts && !pkts)) return XE_EINVAL;
+    if (pkt_stride % 16 || pkt_stride < 16u + 32u * (uint32_t)s.n_inputs) return XE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(pkts) | reinterpret_cast<uintptr_t>(frame)) & 15) return XE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(lost) | reinterpret_cast<uintptr_t>(stats)) & 3) return XE_EINVAL;
+    const int64_t slots = (int64_t)(s.n_time / 4) * (s.n_chan / 8);
+    if (slots > XE_ASSEMBLE_NOALLOC_MAX_SLOTS) return XE_ENOMEM;    // frame larger than the static table
+    int status = XE_OK;
+    uint32_t *owner = asmb::noalloc_owner(&status);
+    if (!owner) return status;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    asmb::Geo g;
+    g.seq0 = seq0;
+    g.n_pkts = n_pkts;
+    g.stride = pkt_stride;
+    g.N = s.n_inputs;
+    g.F = s.n_chan;
+    g.Q = s.n_time / 4;
+    g.G = s.n_chan / 8;
+    g.gps = gps;
+    g.S = g.G / gps;
+    // The table keeps whatever the previous call left in it: reset the slots this frame uses.
+    asmb::init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
+    XE_TRY_CUDA(cudaGetLastError());
+    if (n_pkts) {
+        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats);
+        XE_TRY_CUDA(cudaGetLastError());
+    }
+    const uint64_t blocks = ((uint64_t)n_pkts + (uint64_t)slots + 7) / 8;
+    if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
+    asmb::copy_kernel<<<(unsigned)blocks, 256, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
+    XE_TRY_CUDA(cudaGetLastError());
+    return XE_OK;
+}
