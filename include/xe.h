@@ -206,6 +206,84 @@ int xe_normalize(const int32_t *vis, xe_shape s, uint32_t t_int, const uint32_t 
                  const uint32_t *flag_count, const uint32_t *flag_pairs, float *out,
                  uint32_t *n_out, void *stream);
 
+/* ---------------------------------------------------------------- A7: serving loop (Sec. II) */
+
+/*
+ * A streaming X-engine that keeps packet buffers, frames and visibilities resident on the device
+ * (Sec. II: buffer objects and ring buffers between threads; all memory allocated at start-up and
+ * freed at shutdown, Sec. II; per-stream processing until after correlation, then combined, Sec. II
+ * and II-C; "Data Ready" events and host callbacks, Sec. II-B).
+ *
+ * Producers submit packets of their F-engine stream as they arrive (any order within the reorder
+ * window). The host reads only the 16-byte headers: each run of packets of one frame is copied
+ * directly into that frame's device packet region. A frame closes when more than reorder_window
+ * packets of later frames have arrived on its stream (or at xe_stream_flush); closed frames are
+ * admitted into free device slots, assembled (xe_assemble), correlated together in one batched
+ * persistent launch per admission round (xe_correlate_batched), and normalised by their sample
+ * counts (xe_normalize). Rounds run on a pool of CUDA streams and overlap on the device; a host
+ * callback marks each frame complete. Results stay on the device until released.
+ *
+ * Frame k of a stream covers seq [k*T/4, (k+1)*T/4). All device memory is allocated by
+ * xe_stream_create (within hbm_budget when it is non-zero) and freed by xe_stream_destroy.
+ */
+typedef struct {
+    int32_t n_streams;          /* F-engine streams (stream_id 0..n_streams-1) */
+    int32_t groups_per_stream;  /* channel groups of 8 per stream: F_s = 8 * groups_per_stream */
+    int32_t n_inputs;           /* N, multiple of 16 */
+    int32_t n_time;             /* T per frame, multiple of 4 */
+    uint32_t pkt_stride;        /* bytes per packet record, multiple of 16, >= 16 + 32 N */
+    int32_t reorder_window;     /* packets of later frames after which a frame closes (>= 1) */
+    int32_t ring_frames;        /* device packet regions per stream (frames buffered), >= 2 */
+    int32_t slots;              /* device frame slots (frames in flight or unreleased); 0 = by budget */
+    int32_t max_batch;          /* frames correlated per launch, 1..XE_MAX_JOBS */
+    int32_t n_cuda_streams;     /* CUDA streams rounds are spread over, >= 1 */
+    uint64_t hbm_budget;        /* bytes the runtime may allocate; 0 = no limit */
+    int32_t batch_wait_us;      /* after the first ready frame, wait up to this long for more frames
+                                   to join the round (0 = admit at once) */
+} xe_stream_cfg;
+
+typedef struct xe_stream xe_stream;
+
+typedef struct {
+    int32_t stream_id;
+    int32_t slot;               /* pass back to xe_stream_release */
+    int64_t frame;              /* frame index k */
+    const float *out;           /* device, float [F_s][P][2]: V / n, valid until released */
+    const int32_t *vis;         /* device, int32 [F_s][P][2]: integrated visibilities */
+    const uint32_t *n;          /* device, uint32 [F_s][P]: samples per visibility */
+    const uint32_t *lost;       /* device, uint32 [F_s]: lost samples per channel */
+    const uint32_t *stats;      /* device, uint32 [5]: ok, duplicate, late, early, invalid */
+    uint32_t packets;           /* packets submitted into this frame's region */
+    uint32_t batch;             /* admission round that carried the frame */
+    uint64_t latency_ns;        /* frame closed -> its results complete on the device */
+} xe_result;
+
+typedef struct {
+    uint64_t packets_submitted, packets_late, frames_closed, frames_done, frames_released;
+    uint64_t batches, max_batch_seen;
+    double latency_p50_us, latency_p99_us, latency_max_us;
+    uint64_t device_bytes;
+    int32_t slots;
+} xe_stream_stats_t;
+
+/* Creates the runtime on the current device. Errors: XE_EINVAL, XE_ENOMEM (budget too small for
+ * two slots and the packet regions), XE_ECUDA. */
+int xe_stream_create(const xe_stream_cfg *cfg, xe_stream **out);
+/* Submits n_pkts packets (host memory, arrival order) of one stream. Packets of closed frames count
+ * as late and are dropped. Returns XE_EAGAIN, having consumed nothing, when a packet belongs to a
+ * frame whose packet region is still in use (the device is behind): retry later. Pinned host
+ * memory is copied asynchronously: keep it unchanged until the frames it holds have completed. */
+int xe_stream_submit(xe_stream *s, int32_t stream_id, const void *host_pkts, uint32_t n_pkts);
+/* Closes every open frame (end of data). */
+int xe_stream_flush(xe_stream *s);
+/* Waits up to timeout_ms for the next completed frame (completion order). XE_ETIMEOUT if none. */
+int xe_stream_poll(xe_stream *s, xe_result *out, int32_t timeout_ms);
+/* Returns a completed frame's slot to the pool. */
+int xe_stream_release(xe_stream *s, const xe_result *r);
+int xe_stream_stats(xe_stream *s, xe_stream_stats_t *out);
+/* Waits (bounded) for outstanding device work, then frees everything. */
+int xe_stream_destroy(xe_stream *s);
+
 #ifdef __cplusplus
 }
 #endif

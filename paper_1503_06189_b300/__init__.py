@@ -25,6 +25,8 @@ EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",
     "xe_assemble_workspace_size", "xe_assemble", "xe_assemble_noalloc", "xe_unpack", "xe_correlate_workspace_size",
     "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched", "xe_normalize",
+    "xe_stream_create", "xe_stream_submit", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
+    "xe_stream_stats", "xe_stream_destroy",
 ]
 
 
@@ -57,6 +59,29 @@ class Tune(ctypes.Structure):
                 ("n_ctas", ctypes.c_int32)]
 
 
+class StreamCfg(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("groups_per_stream", ctypes.c_int32), ("n_inputs", ctypes.c_int32),
+                ("n_time", ctypes.c_int32), ("pkt_stride", ctypes.c_uint32), ("reorder_window", ctypes.c_int32),
+                ("ring_frames", ctypes.c_int32), ("slots", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("n_cuda_streams", ctypes.c_int32), ("hbm_budget", ctypes.c_uint64), ("batch_wait_us", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int32), ("slot", ctypes.c_int32), ("frame", ctypes.c_int64),
+                ("out", ctypes.c_void_p), ("vis", ctypes.c_void_p), ("n", ctypes.c_void_p),
+                ("lost", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("packets", ctypes.c_uint32),
+                ("batch", ctypes.c_uint32), ("latency_ns", ctypes.c_uint64)]
+
+
+class StreamStats(ctypes.Structure):
+    _fields_ = [("packets_submitted", ctypes.c_uint64), ("packets_late", ctypes.c_uint64),
+                ("frames_closed", ctypes.c_uint64), ("frames_done", ctypes.c_uint64),
+                ("frames_released", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("max_batch_seen", ctypes.c_uint64), ("latency_p50_us", ctypes.c_double),
+                ("latency_p99_us", ctypes.c_double), ("latency_max_us", ctypes.c_double),
+                ("device_bytes", ctypes.c_uint64), ("slots", ctypes.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libxe.so not built at {LIB_PATH}; run `python -m paper_1503_06189_b300.build`")
@@ -80,6 +105,13 @@ def _load():
     L.xe_correlate_batched_workspace_size.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune)]
     L.xe_correlate_batched.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune), vp, sz, vp]
     L.xe_normalize.argtypes = [vp, Shape, u32, vp, vp, vp, vp, vp, vp]
+    L.xe_stream_create.argtypes = [ctypes.POINTER(StreamCfg), ctypes.POINTER(vp)]
+    L.xe_stream_submit.argtypes = [vp, i32, vp, u32]
+    L.xe_stream_flush.argtypes = [vp]
+    L.xe_stream_poll.argtypes = [vp, ctypes.POINTER(Result), i32]
+    L.xe_stream_release.argtypes = [vp, ctypes.POINTER(Result)]
+    L.xe_stream_stats.argtypes = [vp, ctypes.POINTER(StreamStats)]
+    L.xe_stream_destroy.argtypes = [vp]
     for name in EXPORTED:
         getattr(L, name).restype = getattr(L, name).restype or ctypes.c_int
     return L
@@ -234,3 +266,52 @@ def xe_normalize(vis, shape: Shape, t_int: int, lost, out, n_out=None, flag_coun
                  stream=None):
     _check(_L.xe_normalize(_ptr(vis), shape, t_int, _ptr(lost), _ptr(flag_count), _ptr(flag_pairs), _ptr(out),
                              _ptr(n_out), _stream(stream)), "xe_normalize")
+
+
+# ----------------------------------------------------------------------------- A7
+
+def xe_stream_create(cfg: StreamCfg):
+    """Returns an opaque handle (int) to a serving runtime on the current device."""
+    h = ctypes.c_void_p()
+    _check(_L.xe_stream_create(ctypes.byref(cfg), ctypes.byref(h)), "xe_stream_create")
+    return h.value
+
+
+def xe_stream_submit(handle, stream_id: int, host_pkts, n_pkts: int) -> int:
+    """host_pkts: a pointer (int) or a torch/numpy buffer in host memory. Returns XE_OK or XE_EAGAIN."""
+    if hasattr(host_pkts, "ctypes"):
+        ptr = host_pkts.ctypes.data
+    else:
+        ptr = _ptr(host_pkts)
+    st = _L.xe_stream_submit(handle, stream_id, ptr, n_pkts)
+    if st not in (XE_OK, XE_EAGAIN):
+        raise XeError(st, "xe_stream_submit")
+    return st
+
+
+def xe_stream_flush(handle):
+    _check(_L.xe_stream_flush(handle), "xe_stream_flush")
+
+
+def xe_stream_poll(handle, timeout_ms: int):
+    """Next completed frame as a Result, or None on timeout."""
+    r = Result()
+    st = _L.xe_stream_poll(handle, ctypes.byref(r), timeout_ms)
+    if st == XE_ETIMEOUT:
+        return None
+    _check(st, "xe_stream_poll")
+    return r
+
+
+def xe_stream_release(handle, result: Result):
+    _check(_L.xe_stream_release(handle, ctypes.byref(result)), "xe_stream_release")
+
+
+def xe_stream_stats(handle) -> StreamStats:
+    o = StreamStats()
+    _check(_L.xe_stream_stats(handle, ctypes.byref(o)), "xe_stream_stats")
+    return o
+
+
+def xe_stream_destroy(handle):
+    _check(_L.xe_stream_destroy(handle), "xe_stream_destroy")

@@ -26,13 +26,14 @@ struct Geo {
     uint64_t seq0;
     uint32_t n_pkts, stride;
     int32_t N, F, Q, G, gps, S;
+    uint32_t stream_base = 0;    // header stream ids [stream_base, stream_base + S) map to this frame
 };
 
 enum Class { kOk = 0, kLate = 2, kEarly = 3, kInvalid = 4 };
 
 __device__ __forceinline__ int classify(const uint8_t *pkts, const Geo &g, uint32_t k, int &slot, int &grp) {
     const uint4 h = __ldg(reinterpret_cast<const uint4 *>(pkts + (size_t)k * g.stride));
-    const uint32_t sid = h.x & 0xFFFFu, cg = h.x >> 16;
+    const uint32_t sid = (h.x & 0xFFFFu) - g.stream_base, cg = h.x >> 16;
     const uint64_t seq = (static_cast<uint64_t>(h.w) << 32) | h.z;
     if (sid >= (uint32_t)g.S || cg >= (uint32_t)g.gps) return kInvalid;
     if (seq < g.seq0) return kLate;
@@ -114,6 +115,17 @@ size_t xe_assemble_workspace_size(xe_shape s) {
 int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
                 xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost, uint32_t *stats, void *ws,
                 size_t ws_bytes, void *stream) {
+    return xe::assemble_streams(pkts, n_pkts, pkt_stride, seq0, gps, 0, s, frame, filled, lost, stats, ws, ws_bytes,
+                                static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+// xe_assemble for the frame of some streams: packets whose header stream id is stream_base + s map
+// to the frame's stream s (the serving loop assembles each F-engine stream into its own frame).
+int xe::assemble_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                         uint32_t stream_base, xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost,
+                         uint32_t *stats, void *ws, size_t ws_bytes, cudaStream_t st) {
     if (!valid_shape(s) || s.n_time < 4 || s.n_time % 4 || s.n_chan % 8 || gps < 1 || (s.n_chan / 8) % gps)
         return XE_EINVAL;
     if (!frame || !filled || !lost || !stats || (n_pkts && !pkts)) return XE_EINVAL;
@@ -122,8 +134,8 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
     if ((reinterpret_cast<uintptr_t>(lost) | reinterpret_cast<uintptr_t>(stats) | reinterpret_cast<uintptr_t>(ws)) & 3)
         return XE_EINVAL;
     if (!ws || ws_bytes < xe_assemble_workspace_size(s)) return XE_ENOMEM;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     asmb::Geo g;
+    g.stream_base = stream_base;
     g.seq0 = seq0;
     g.n_pkts = n_pkts;
     g.stride = pkt_stride;
@@ -148,8 +160,6 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
-
-}  // extern "C"
 
 // ---------------------------------------------------------------------------- allocation-free variant
 // xe_assemble_noalloc runs the same three kernels as xe_assemble, but its owner table lives in a

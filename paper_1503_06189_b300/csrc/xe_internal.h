@@ -42,6 +42,11 @@ int encode_tiled(CUtensorMap *map, CUtensorMapDataType dtype, uint32_t rank, voi
 XE_HD inline int64_t npairs(int64_t n) { return n * (n + 1) / 2; }
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// xe_assemble with header stream ids offset by stream_base (see xe_assemble.cu).
+int assemble_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                     uint32_t stream_base, xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost,
+                     uint32_t *stats, void *ws, size_t ws_bytes, cudaStream_t st);
+
 inline bool valid_shape(const xe_shape &s) {
     return s.n_inputs >= 16 && s.n_inputs <= 4096 && s.n_inputs % 16 == 0 && s.n_chan >= 1 &&
            s.n_time >= 0;
