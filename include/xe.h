@@ -174,6 +174,7 @@ typedef struct {
     int32_t *vis;          /* device, int32 [F][P][2] */
     xe_shape s;
     int32_t accumulate;    /* 0: write, 1: add */
+    int32_t max_strip;     /* 1..4: tile width of this job's work items; 0 = the call's tune */
 } xe_job;
 
 /*

@@ -8,6 +8,7 @@ loops) through ctypes; the C source is built by :func:`build` with gcc.
 Function / paper passage:
   sample          one 4+4-bit byte -> (re, im)                       Sec. I
   correlate       V_f[i,j] = sum_t x_i conj(x_j), i <= j              Sec. I, Sec. II-B
+  correlate_pairs the same for selected (i, j) of one channel          Sec. I, Sec. II-B
   assemble        packets -> frame, zero-fill, reorder, dedup         Sec. II-A.2
   counts_from_mask      n_ij by brute force over the sample mask      Sec. II-C
   counts_from_counters  n_ij by the loss / flag / intersection counters  Sec. II-C
@@ -66,6 +67,8 @@ class Oracle:
         L.xo_npairs.restype = ctypes.c_int64
         L.xo_npairs.argtypes = [ctypes.c_int]
         L.xo_sample.argtypes = [ctypes.c_uint8, P(ctypes.c_int), P(ctypes.c_int)]
+        L.xo_correlate_pairs.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
         self.L = L
 
     def threads(self) -> int:
@@ -92,6 +95,16 @@ class Oracle:
         if st == EINVAL:
             raise ValueError("xo_correlate: invalid arguments")
         return vis, st
+
+    def correlate_pairs(self, frame: np.ndarray, f: int, pairs) -> np.ndarray:
+        """Visibilities of channel f for the given (i, j), i <= j, pairs: int64 [n][2] (re, im)."""
+        frame = np.ascontiguousarray(frame, dtype=np.uint8)
+        T, F, N = frame.shape
+        pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+        out = np.zeros((pr.shape[0], 2), dtype=np.int64)
+        if self.L.xo_correlate_pairs(_ptr(frame), N, F, T, f, _ptr(pr), pr.shape[0], _ptr(out)) != OK:
+            raise ValueError("xo_correlate_pairs: invalid arguments")
+        return out
 
     def assemble(self, pkts: np.ndarray, seq0: int, gps: int, n_inputs: int, n_chan: int, n_time: int,
                  lost: np.ndarray | None = None, stats: np.ndarray | None = None):
@@ -171,6 +184,10 @@ def sample(b: int):
 
 def correlate(frame, f0: int = 0, nf=None):
     return default().correlate(frame, f0, nf)
+
+
+def correlate_pairs(frame, f, pairs):
+    return default().correlate_pairs(frame, f, pairs)
 
 
 def assemble(pkts, seq0, gps, n_inputs, n_chan, n_time, lost=None, stats=None):

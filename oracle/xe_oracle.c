@@ -89,6 +89,33 @@ int xo_correlate(const uint8_t *frame, int N, int F, int T, int f0, int nf, int6
 }
 
 /*
+ * Selected visibilities of one channel f, straight from the definition (for sampled checks of
+ * frames too large to correlate in full on the CPU). pairs: int32 [n][2] with i <= j; vis: int64
+ * [n][2].
+ */
+int xo_correlate_pairs(const uint8_t *frame, int N, int F, int T, int f, const int32_t *pairs, int n,
+                       int64_t *vis) {
+    if (!frame || !pairs || !vis || N <= 0 || F <= 0 || T < 0 || f < 0 || f >= F || n < 0) return XO_EINVAL;
+    for (int q = 0; q < n; ++q)
+        if (pairs[2 * q] < 0 || pairs[2 * q] > pairs[2 * q + 1] || pairs[2 * q + 1] >= N) return XO_EINVAL;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int q = 0; q < n; ++q) {
+        const int i = pairs[2 * q], j = pairs[2 * q + 1];
+        int64_t sr = 0, si = 0;
+        for (int t = 0; t < T; ++t) {
+            int ai, bi, aj, bj;
+            xo_sample(frame[((size_t)t * F + f) * N + i], &ai, &bi);
+            xo_sample(frame[((size_t)t * F + f) * N + j], &aj, &bj);
+            sr += (int64_t)ai * aj + (int64_t)bi * bj;
+            si += (int64_t)bi * aj - (int64_t)ai * bj;
+        }
+        vis[2 * q] = sr;
+        vis[2 * q + 1] = si;
+    }
+    return XO_OK;
+}
+
+/*
  * Frame assembly from UDP packets (Sec. II-A.2: loss zero-fill, reorder by sequence number,
  * duplicates ignored), replayed packet by packet in arrival order.
  *   pkts      n_pkts records of pkt_stride bytes: 16-byte header then [4][8][N] payload

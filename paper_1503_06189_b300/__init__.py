@@ -51,7 +51,8 @@ class Shape(ctypes.Structure):
 
 
 class Job(ctypes.Structure):
-    _fields_ = [("frame", ctypes.c_void_p), ("vis", ctypes.c_void_p), ("s", Shape), ("accumulate", ctypes.c_int32)]
+    _fields_ = [("frame", ctypes.c_void_p), ("vis", ctypes.c_void_p), ("s", Shape), ("accumulate", ctypes.c_int32),
+                ("max_strip", ctypes.c_int32)]
 
 
 class Tune(ctypes.Structure):
@@ -234,9 +235,12 @@ def xe_correlate(frame, shape: Shape, vis, accumulate: bool, ws, stream=None):
 
 
 def _jobs(jobs):
+    """jobs: (frame, vis, Shape, accumulate) or (frame, vis, Shape, accumulate, max_strip) tuples."""
     arr = (Job * len(jobs))()
-    for k, (frame, vis, shape, acc) in enumerate(jobs):
-        arr[k] = Job(_ptr(frame), _ptr(vis), shape, 1 if acc else 0)
+    for k, j in enumerate(jobs):
+        frame, vis, shape, acc = j[:4]
+        ms = j[4] if len(j) > 4 else 0
+        arr[k] = Job(_ptr(frame), _ptr(vis), shape, 1 if acc else 0, int(ms))
     return arr
 
 

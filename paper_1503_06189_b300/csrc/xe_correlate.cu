@@ -60,11 +60,12 @@ struct Job {                 // 128-byte aligned through its CUtensorMap
     int32_t k_tiles;         // ceil(T / 128)
     int32_t item_begin;      // first global work-item index of this job
     int32_t pw;              // fused: bytes per packed row in shared memory (min(64, N))
+    int32_t max_strip;       // tiles per work item along a row (1..4) for this job
 };
 
 struct Params {
     Job jobs[XE_MAX_JOBS];
-    int32_t n_jobs, n_items, max_strip, k_flush_tiles;
+    int32_t n_jobs, n_items, k_flush_tiles;
     int32_t op_stages, pk_stages, slots, n_acc;
     int *status;
     int *counter;            // work-item counter, zero at launch
@@ -127,7 +128,7 @@ __device__ __forceinline__ Item decode_item(const Params &p, int g) {
     const int l = g - jb.item_begin;
     it.job = j;
     it.f = l / jb.strips;
-    decode_strip(l % jb.strips, jb.nb, p.max_strip, it.rb, it.cb0, it.w);
+    decode_strip(l % jb.strips, jb.nb, jb.max_strip, it.rb, it.cb0, it.w);
     const bool off_diag = it.rb < it.cb0;
     it.nblk = it.w + (off_diag ? 1 : 0);
     it.a_slot = off_diag ? it.w : 0;
@@ -716,7 +717,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
     int *counter = reinterpret_cast<int *>(base);
     uint8_t *ybase = base + kWsHeader;
-    int items = 0, nj = 0;
+    int items = 0, nj = 0, ms_max = 1;
     for (int j = 0; j < n_jobs; ++j) {
         const xe_shape &s = jobs[j].s;
         const JobGeom g = geom(s, engine);
@@ -761,7 +762,10 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         d.n_time = s.n_time;
         d.accumulate = jobs[j].accumulate ? 1 : 0;
         d.nb = g.nb;
-        d.strips = strips_per_channel(g.nb, tune.max_strip);
+        d.max_strip = jobs[j].max_strip > 0 ? jobs[j].max_strip : tune.max_strip;
+        if (d.max_strip > 4) return XE_EINVAL;
+        ms_max = std::max(ms_max, d.max_strip);
+        d.strips = strips_per_channel(g.nb, d.max_strip);
         d.k_tiles = g.k_tiles;
         d.item_begin = items;
         const int64_t add = (int64_t)d.strips * s.n_chan;
@@ -771,10 +775,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     if (nj == 0) return XE_OK;
     hp.n_jobs = nj;
     hp.n_items = items;
-    hp.max_strip = tune.max_strip;
     hp.k_flush_tiles = tune.k_flush / kt_of(engine);
-    hp.slots = tune.max_strip == 1 ? 2 : (tune.max_strip == 2 ? 3 : 4);
-    hp.n_acc = tune.max_strip <= 2 ? 2 : 1;
+    hp.slots = ms_max == 1 ? 2 : (ms_max == 2 ? 3 : 4);     // operand blocks per stage for the widest strip
+    hp.n_acc = ms_max <= 2 ? 2 : 1;                        // TMEM accumulators (each <= 256 columns)
     hp.status = status;
     hp.counter = counter;
     hp.limit_ns = wait_limit_ns();
@@ -814,13 +817,13 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
 
 size_t xe_correlate_workspace_size(xe_shape s) {
     if (!valid_shape(s)) return 0;
-    xe_job j{nullptr, nullptr, s, 0};
+    xe_job j{nullptr, nullptr, s, 0, 0};
     return corr::batched_ws(&j, 1, corr::engine_of(XE_ENGINE_FUSED));
 }
 
 int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate, void *ws, size_t ws_bytes,
                  void *stream) {
-    xe_job j{frame, vis, s, accumulate ? 1 : 0};
+    xe_job j{frame, vis, s, accumulate ? 1 : 0, 0};
     return corr::run_batched(&j, 1, nullptr, ws, ws_bytes, static_cast<cudaStream_t>(stream));
 }
 

@@ -229,7 +229,7 @@ static void scheduler(xe_stream *rt) {
                 cudaEventRecord(reg->consumed, st);
                 reg->issued = true;
             }
-            jobs.push_back(xe_job{sl.frame, sl.vis, shape, 0});
+            jobs.push_back(xe_job{sl.frame, sl.vis, shape, 0, 0});
         }
         int e = xe_correlate_batched(jobs.data(), (int32_t)jobs.size(), nullptr, ws, rt->ws_c_bytes, st);
         if (e) err = e;
@@ -275,7 +275,7 @@ int xe_stream_create(const xe_stream_cfg *cfg, xe_stream **out) {
     rt->cap = (uint32_t)(pkts_per_frame + pkts_per_frame / 4 + 64);   // room for duplicates
     const xe_shape shape{c.n_inputs, rt->Fs, c.n_time};
     rt->ws_a_bytes = round_up(xe_assemble_workspace_size(shape), 256);
-    xe_job probe{nullptr, nullptr, shape, 0};
+    xe_job probe{nullptr, nullptr, shape, 0, 0};
     rt->ws_c_bytes = round_up(xe_correlate_batched_workspace_size(&probe, 1, nullptr), 1024);
     if (!rt->ws_a_bytes || !rt->ws_c_bytes) return XE_EINVAL;
 

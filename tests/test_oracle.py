@@ -109,6 +109,22 @@ def pin_library_gram(o, seed=12):
         np.testing.assert_array_equal(vis[f, :, 1], Vim[iu])
 
 
+def pin_pairs(o):
+    """Selected pairs against Python complex brute force, and equal to the full triangle's entries."""
+    rng = np.random.default_rng(17)
+    fr = rng.integers(0, 256, (41, 3, 9), dtype=np.uint8)
+    V = brute_full(fr)
+    pairs = [(0, 0), (0, 8), (3, 5), (8, 8), (2, 7)]
+    got = o.correlate_pairs(fr, 2, pairs)
+    for (i, j), g in zip(pairs, got):
+        assert complex(g[0], g[1]) == V[2][i][j]
+    full, _ = o.correlate(synth.uniform_frame(32, 2, 300, 18))
+    fr2 = synth.uniform_frame(32, 2, 300, 18)
+    pr = [(i, j) for i in range(0, 32, 5) for j in range(i, 32, 7)]
+    got = o.correlate_pairs(fr2, 1, pr)
+    np.testing.assert_array_equal(got, full[1, [o.pidx(i, j, 32) for i, j in pr]])
+
+
 def pin_subset_channels(o):
     fr = synth.uniform_frame(16, 6, 300, 13)
     full, _ = o.correlate(fr)
@@ -313,7 +329,7 @@ def pin_table1_geometry(o):
     assert round(out_sys / 1e6, 1) == g["output_per_10s"]["system"]
 
 
-PINS = [pin_sample_decode, pin_pidx_bijection, pin_brute_force, pin_library_gram, pin_subset_channels,
+PINS = [pin_sample_decode, pin_pidx_bijection, pin_brute_force, pin_pairs, pin_library_gram, pin_subset_channels,
         pin_autocorrelation, pin_constant_input, pin_single_source, pin_overflow_bound,
         pin_assembly_basic, pin_assembly_permutation, pin_assembly_loss_and_dups, pin_assembly_window,
         pin_counts_counters_equal_mask, pin_normalize, pin_table1_geometry]
