@@ -138,6 +138,7 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
 #define XE_ENGINE_UNPACKED 1    /* A2 unpack to HBM (MN-major), then the tcgen05 GEMM reads it */
 #define XE_ENGINE_FUSED 2       /* the GEMM loads packed bytes and expands them in shared memory */
 #define XE_ENGINE_UNPACKED_K 3  /* A2 unpack to HBM transposed (K-major), then the GEMM */
+#define XE_ENGINE_FUSED_PAIR 4  /* as FUSED, on CTA pairs: 256x256 blocks with M = 256 pair MMAs */
 
 typedef struct {
     int32_t engine;      /* XE_ENGINE_* */

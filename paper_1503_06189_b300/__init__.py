@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(_HERE, "libxe.so")
 XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ENOMEM, XE_ECUDA, XE_ETIMEOUT, XE_EAGAIN = 0, -1, -2, -3, -4, -5, -6
 XE_MAX_TIME = (1 << 24) - 1
 XE_MAX_JOBS = 64
-XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K = 0, 1, 2, 3
+XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K, XE_ENGINE_FUSED_PAIR = 0, 1, 2, 3, 4
 
 EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",

@@ -49,7 +49,7 @@ constexpr int kDefaultKFlush = 1 << 15;
 constexpr int kMaxKFlush = 1 << 15;
 constexpr int kConvWarps = 8;
 
-enum Engine { kUnpackedK = 0, kUnpackedMN = 1, kFusedMN = 2 };
+enum Engine { kUnpackedK = 0, kUnpackedMN = 1, kFusedMN = 2, kFusedPair = 3 };
 
 struct Job {                 // 128-byte aligned through its CUtensorMap
     CUtensorMap tmap;        // operand map (unpacked engines) or packed frame map (fused)
@@ -601,6 +601,328 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
     if (warp == 1) dev::tmem_dealloc(tmem, kTmemCols);
 }
 
+// ----------------------------------------------------------------------------- pair engine (cta_group::2)
+//
+// FUSED_PAIR: a cluster of two CTAs on two SMs computes 256x256 blocks (R, C), C >= R, of a
+// channel's Gram matrix with M = 256 tensor-core MMAs whose operands are split across the pair:
+// CTA r holds A rows 256R + 128r .. +128 (operand block 2R + r) and B columns 256C + 128r .. +128
+// (block 2C + r) in its own shared memory, and receives D rows 256R + 128r .. +128 x all 256
+// columns in its own tensor memory. Each SM thus reads half of B per MAC and each converted block
+// feeds twice the MACs of the single-CTA engine. On a diagonal block (R = C) the A and B halves of
+// a CTA are the same block. Both CTAs walk the same static item sequence (item g = pair + k *
+// pairs, channel-major); converters and epilogue warps of both CTAs arrive on the even CTA's
+// barriers, and the even CTA's single MMA thread commits to both CTAs.
+
+constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA: A, B
+
+__device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C) {
+    int j = 0;
+    while (j + 1 < p.n_jobs && g >= p.jobs[j + 1].item_begin) ++j;
+    const Job &jb = p.jobs[j];
+    const int l = g - jb.item_begin;
+    job = j;
+    f = l / jb.strips;
+    int q = l % jb.strips;
+    const int S2 = jb.nb;                     // 256-row super-blocks
+    for (R = 0; R < S2; ++R) {
+        if (q < S2 - R) break;
+        q -= S2 - R;
+    }
+    C = R + q;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (kConvWarp0 + kConvWarps), 1)
+    correlate_pair_kernel(const __grid_constant__ Params p) {
+    constexpr int kKt = kKtMN;
+    constexpr int kOpSlotBytes = kBlk * kKt;
+    constexpr int kPkSlotBytes = 64 * kKt;
+    constexpr int kTasks = kKt * 4 / (32 * kConvWarps);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int op_stage_bytes = kPairSlots * kOpSlotBytes;
+    const int pk_stage_bytes = kPairSlots * kPkSlotBytes;
+    uint8_t *op_ring = smem;
+    uint8_t *pk_ring = smem + p.op_stages * op_stage_bytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(pk_ring + p.pk_stages * pk_stage_bytes);
+    uint64_t *op_full = bars;                       // [op_stages] even CTA: both CTAs' converters
+    uint64_t *op_empty = op_full + p.op_stages;     // [op_stages] pair MMAs done (multicast commit)
+    uint64_t *pk_full = op_empty + p.op_stages;     // [pk_stages] local TMA
+    uint64_t *pk_empty = pk_full + p.pk_stages;     // [pk_stages] local converters
+    uint64_t *acc_full = pk_empty + p.pk_stages;    // [2] pair MMAs of a segment done (multicast)
+    uint64_t *acc_empty = acc_full + 2;             // [2] even CTA: both CTAs' epilogues drained
+    uint64_t *conv_done = acc_empty + 2;            // [op_stages] local: this CTA's converters finished
+    uint64_t *epi_done = conv_done + p.op_stages;   // [2] local: this CTA's epilogue drained
+    uint64_t *done = epi_done + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = dev::cluster_ctarank();
+    const bool leader = rank == 0;
+    const int pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
+    const uint32_t op_base = dev::smem_u32(op_ring);
+    const uint32_t pk_base = dev::smem_u32(pk_ring);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < p.op_stages; ++s) {
+            dev::mbar_init(&op_full[s], 2);         // one arrival per CTA of the pair
+            dev::mbar_init(&op_empty[s], 1);
+        }
+        for (int s = 0; s < p.pk_stages; ++s) {
+            dev::mbar_init(&pk_full[s], 1);
+            dev::mbar_init(&pk_empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            dev::mbar_init(&acc_full[a], 1);
+            dev::mbar_init(&acc_empty[a], 2);
+            dev::mbar_init(&epi_done[a], kEpiWarps);
+        }
+        for (int s = 0; s < p.op_stages; ++s) dev::mbar_init(&conv_done[s], kConvWarps);
+        dev::mbar_init(done, 1);
+        *abort_flag = 0;
+        dev::fence_mbar_init();
+        for (int j = 0; j < p.n_jobs; ++j) dev::prefetch_tmap(&p.jobs[j].tmap);
+    }
+    if (warp == 1) {
+        dev::tmem_alloc_pair(tmem_slot, kTmemCols);
+        dev::tmem_relinquish_pair();
+    }
+    dev::tc_fence_before();
+    __syncthreads();
+    dev::cluster_sync();                            // barriers of both CTAs initialised
+    dev::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto wait = [&](uint64_t *bar, uint32_t parity, bool cluster_scope) -> bool {
+        auto test = [&] { return cluster_scope ? dev::mbar_try_wait_cluster(bar, parity) : dev::mbar_try_wait(bar, parity); };
+        if (test()) return true;
+        const uint64_t t0 = dev::globaltimer_ns();
+        for (uint32_t it = 1;; ++it) {
+            if (test()) return true;
+            if ((it & 127u) == 0) {
+                if (*abort_flag) return false;
+                if (dev::globaltimer_ns() - t0 > p.limit_ns) {
+                    *abort_flag = 1;
+                    atomicExch(p.status, XE_ETIMEOUT);
+                    return false;
+                }
+            }
+        }
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------------------- TMA producer (both CTAs)
+            uint32_t s = 0, ph = 0, issued = 0, issued_parity = 0;
+            bool ok = true;
+            for (int g = pair; g < p.n_items && ok; g += n_pairs) {
+                int job, f, R, C;
+                decode_pair_item(p, g, job, f, R, C);
+                const Job &jb = p.jobs[job];
+                const int nblk = R == C ? 1 : 2;
+                const uint32_t tx = nblk * jb.pw * kKt;
+                for (int kt = 0; kt < jb.k_tiles; ++kt) {
+                    if (!wait(&pk_empty[s], ph ^ 1, false)) { ok = false; break; }
+                    dev::mbar_arrive_expect_tx(&pk_full[s], tx);
+                    dev::tma_load_3d(pk_base + s * pk_stage_bytes, &jb.tmap, &pk_full[s], (2 * R + rank) * 64, f, kt * kKt);
+                    if (nblk == 2)
+                        dev::tma_load_3d(pk_base + s * pk_stage_bytes + kPkSlotBytes, &jb.tmap, &pk_full[s],
+                                         (2 * C + rank) * 64, f, kt * kKt);
+                    issued |= 1u << s;
+                    issued_parity = (issued_parity & ~(1u << s)) | (ph << s);
+                    if (++s == (uint32_t)p.pk_stages) { s = 0; ph ^= 1; }
+                }
+            }
+            for (int q = 0; q < p.pk_stages; ++q)
+                if (issued & (1u << q)) dev::mbar_wait(&pk_full[q], (issued_parity >> q) & 1u, p.limit_ns);
+        } else if (lane == 1) {
+            // ---------------------------------------------------------------- converter forwarder
+            // once all converter warps of this CTA finished a stage: free the packed stage and tell
+            // the even CTA's MMA thread (one arrival per CTA and stage)
+            uint32_t ps = 0, os = 0, oph = 0;
+            bool ok = true;
+            for (int g = pair; g < p.n_items && ok; g += n_pairs) {
+                int job, f, R, C;
+                decode_pair_item(p, g, job, f, R, C);
+                for (int kt = 0; kt < p.jobs[job].k_tiles; ++kt) {
+                    if (!wait(&conv_done[os], oph, false)) { ok = false; break; }
+                    dev::mbar_arrive(&pk_empty[ps]);
+                    dev::mbar_arrive_remote(&op_full[os], 0);
+                    if (++ps == (uint32_t)p.pk_stages) ps = 0;
+                    if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
+                }
+            }
+        } else if (lane == 2) {
+            // ---------------------------------------------------------------- epilogue forwarder
+            uint32_t acc = 0, acc_ph = 0;
+            bool ok = true;
+            for (int g = pair; g < p.n_items && ok; g += n_pairs) {
+                int job, f, R, C;
+                decode_pair_item(p, g, job, f, R, C);
+                for (int k0 = 0; k0 < p.jobs[job].k_tiles; k0 += p.k_flush_tiles) {
+                    if (!wait(&epi_done[acc], (acc_ph >> acc) & 1u, false)) { ok = false; break; }
+                    dev::mbar_arrive_remote(&acc_empty[acc], 0);
+                    acc_ph ^= 1u << acc;
+                    acc ^= 1u;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ---------------------------------------------------------------- pair MMA issuer (even CTA)
+            constexpr uint32_t idesc = dev::idesc_e5m2_f32_mn(256, 256);
+            uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
+            bool ok = true;
+            for (int g = pair; g < p.n_items && ok; g += n_pairs) {
+                int job, f, R, C;
+                decode_pair_item(p, g, job, f, R, C);
+                const Job &jb = p.jobs[job];
+                const uint32_t b_slot = R == C ? 0u : 1u;
+                for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles) {
+                    const int k1 = min(jb.k_tiles, k0 + p.k_flush_tiles);
+                    if (!wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u, false)) { ok = false; break; }
+                    dev::tc_fence_after();
+                    for (int kt = k0; kt < k1; ++kt) {
+                        if (!wait(&op_full[s], ph, false)) { ok = false; break; }
+                        dev::tc_fence_after();
+                        const uint32_t sb = op_base + s * op_stage_bytes;
+#pragma unroll
+                        for (int kk = 0; kk < kKt / 32; ++kk) {
+                            const uint64_t ad = dev::sdesc_mn_sw128(sb + kk * 4096, kOpSlotBytes);
+                            const uint64_t bd = dev::sdesc_mn_sw128(sb + b_slot * kOpSlotBytes + kk * 4096, kOpSlotBytes);
+                            dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, bd, idesc, (kt > k0 || kk > 0) ? 1u : 0u);
+                        }
+                        dev::tc_commit_pair_multicast(&op_empty[s], 3);
+                        if (++s == (uint32_t)p.op_stages) { s = 0; ph ^= 1; }
+                    }
+                    if (!ok) break;
+                    dev::tc_commit_pair_multicast(&acc_full[acc], 3);
+                    acc_ph ^= 1u << acc;
+                    acc ^= 1u;
+                }
+            }
+            dev::tc_commit_pair_multicast(done, 1);
+            dev::mbar_wait(done, 0, p.limit_ns);
+        }
+    } else if (warp < kConvWarp0) {
+        // -------------------------------------------------------------------- epilogue (both CTAs)
+        using O = Order<true>;
+        const int q = warp & 3;
+        const int half = (warp - kEpiWarp0) >> 2;
+        const int m = q * 32 + lane;
+        const bool im_row = O::comp_of(m) != 0;
+        uint32_t acc = 0, acc_ph = 0;
+        bool ok = true;
+        for (int g = pair; g < p.n_items && ok; g += n_pairs) {
+            int job, f, R, C;
+            decode_pair_item(p, g, job, f, R, C);
+            const Job &jb = p.jobs[job];
+            const int N = jb.n_inputs;
+            const int rb = 2 * R + (int)rank, cb0 = 2 * C;
+            const int i = rb * (kBlk / 2) + O::input_of(m);
+            const bool i_ok = i < N;
+            const int64_t prow = (int64_t)i * N - (int64_t)i * (i - 1) / 2 - i;
+            int32_t *vis_f = jb.vis + (size_t)f * (size_t)npairs(N) * 2;
+            const int n_chunks = 2 * (kBlk / 32);
+            for (int k0 = 0; k0 < jb.k_tiles; k0 += p.k_flush_tiles) {
+                if (!wait(&acc_full[acc], (acc_ph >> acc) & 1u, false)) { ok = false; break; }
+                dev::tc_fence_after();
+                const bool add = jb.accumulate || k0 > 0;
+                const uint32_t tb = tmem + acc * 256u + (uint32_t(q * 32) << 16);
+                auto jb_of = [&](int ck) { return (cb0 * kBlk + ck * 32) / 2 + (im_row ? 8 : 0); };
+                int2 old[8], nxt[8];
+                int ck = half;
+                if (add && ck < n_chunks) load_old(vis_f, prow, i, jb_of(ck), N, i_ok, old);
+                else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) old[k] = make_int2(0, 0);
+                }
+#pragma unroll 1
+                for (; ck < n_chunks; ck += 2) {
+                    const bool more = ck + 2 < n_chunks;
+                    if (add && more) load_old(vis_f, prow, i, jb_of(ck + 2), N, i_ok, nxt);
+                    int vr[8], vi[8];
+                    combine_chunk<true>(tb + ck * 32, im_row, vr, vi);
+                    store_vis(vis_f, prow, i, jb_of(ck), N, i_ok, vr, vi, old);
+                    if (add && more) {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) old[k] = nxt[k];
+                    }
+                }
+                dev::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) dev::mbar_arrive(&epi_done[acc]);
+                acc_ph ^= 1u << acc;
+                acc ^= 1u;
+            }
+        }
+    } else {
+        // -------------------------------------------------------------------- converters (both CTAs)
+        const int ctid = threadIdx.x - 32 * kConvWarp0;
+        uint32_t dst0[kTasks], dst1[kTasks];
+#pragma unroll
+        for (int u = 0; u < kTasks; ++u) {
+            const int r = ctid + 32 * kConvWarps * u, t = r >> 2, c = r & 3;
+            dst0[u] = t * 128 + (((2 * c) ^ (t & 7)) << 4);
+            dst1[u] = t * 128 + (((2 * c + 1) ^ (t & 7)) << 4);
+        }
+        uint32_t ps = 0, pph = 0, os = 0, oph = 0;
+        bool ok = true;
+        for (int g = pair; g < p.n_items && ok; g += n_pairs) {
+            int job, f, R, C;
+            decode_pair_item(p, g, job, f, R, C);
+            const Job &jb = p.jobs[job];
+            const int nblk = R == C ? 1 : 2;
+            uint32_t src[kTasks];
+            bool have[kTasks];
+#pragma unroll
+            for (int u = 0; u < kTasks; ++u) {
+                const int r = ctid + 32 * kConvWarps * u, t = r >> 2, c = r & 3;
+                src[u] = t * jb.pw + 16 * c;
+                have[u] = 16 * c < jb.pw;
+            }
+            for (int kt = 0; kt < jb.k_tiles; ++kt) {
+                if (!wait(&pk_full[ps], pph, false)) { ok = false; break; }
+                if (!wait(&op_empty[os], oph ^ 1, false)) { ok = false; break; }
+                const uint32_t pk = pk_base + ps * pk_stage_bytes;
+                const uint32_t op = op_base + os * op_stage_bytes;
+#pragma unroll
+                for (int b = 0; b < kPairSlots; ++b) {
+                    if (b < nblk) {
+#pragma unroll
+                        for (int u = 0; u < kTasks; ++u) {
+                            uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+                            if (have[u]) {
+                                uint4 v;
+                                asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                                             : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                                             : "r"(pk + b * kPkSlotBytes + src[u]));
+                                dev::expand16_e5m2(v, lo, hi);
+                            }
+                            const uint32_t row = op + b * kOpSlotBytes;
+                            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                                         ::"r"(row + dst0[u]), "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w));
+                            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                                         ::"r"(row + dst1[u]), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
+                        }
+                    }
+                }
+                dev::fence_proxy_async_smem();                // operand visible to the tensor core
+                __syncwarp();
+                if (lane == 0) dev::mbar_arrive(&conv_done[os]);
+                if (++ps == (uint32_t)p.pk_stages) { ps = 0; pph ^= 1; }
+                if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
+            }
+        }
+    }
+
+    dev::tc_fence_before();
+    __syncthreads();
+    dev::cluster_sync();                            // no CTA leaves while its pair may still signal it
+    dev::tc_fence_after();
+    if (warp == 1) dev::tmem_dealloc_pair(tmem, kTmemCols);
+}
+
 // ----------------------------------------------------------------------------- host side
 
 struct JobGeom {
@@ -616,7 +938,7 @@ static JobGeom geom(const xe_shape &s, int engine) {
     g.nb = g.R / kBlk;
     g.ldy = round_up(std::max<int64_t>(s.n_time, 1), kKtMax);
     g.k_tiles = (int)((s.n_time + kt - 1) / kt);
-    g.y_bytes = engine == kFusedMN ? 0 : (size_t)round_up((int64_t)s.n_chan * g.R * g.ldy, 1024);
+    g.y_bytes = (engine == kFusedMN || engine == kFusedPair) ? 0 : (size_t)round_up((int64_t)s.n_chan * g.R * g.ldy, 1024);
     return g;
 }
 
@@ -632,6 +954,7 @@ static int engine_of(int api_engine) {
         case XE_ENGINE_UNPACKED: return kUnpackedMN;
         case XE_ENGINE_FUSED: return kFusedMN;
         case XE_ENGINE_UNPACKED_K: return kUnpackedK;
+        case XE_ENGINE_FUSED_PAIR: return kFusedPair;
         default: return -1;
     }
 }
@@ -696,6 +1019,37 @@ static int launch_gemm(const Params &hp, int ctas, int smem, cudaStream_t st) {
     return XE_OK;
 }
 
+// Pair engine: as many 2-CTA clusters as can be resident at once (each CTA fills an SM), one per
+// work item at most.
+static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaStream_t st) {
+    static int max_pairs[64] = {};
+    int dev = 0;
+    XE_TRY_CUDA(cudaGetDevice(&dev));
+    if (dev >= 64) return XE_EINVAL;
+    if (!max_pairs[dev]) {
+        XE_TRY_CUDA(cudaFuncSetAttribute(correlate_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * sm_count() / 2, 1, 1);
+        cfg.blockDim = dim3(32 * (kConvWarp0 + kConvWarps), 1, 1);
+        cfg.dynamicSmemBytes = kSmemMax;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        XE_TRY_CUDA(cudaOccupancyMaxActiveClusters(&n, correlate_pair_kernel, &cfg));
+        max_pairs[dev] = std::max(1, n);
+    }
+    int pairs = std::min(items, max_pairs[dev]);
+    if (n_ctas > 0) pairs = std::max(1, std::min(pairs, n_ctas / 2));
+    correlate_pair_kernel<<<2 * pairs, 32 * (kConvWarp0 + kConvWarps), smem, st>>>(hp);
+    XE_TRY_CUDA(cudaGetLastError());
+    return XE_OK;
+}
+
 static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, void *ws, size_t ws_bytes,
                        cudaStream_t st) {
     if (!jobs || n_jobs < 1 || n_jobs > XE_MAX_JOBS) return XE_EINVAL;
@@ -730,7 +1084,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         }
         Job &d = hp.jobs[nj++];
         int enc;
-        if (engine == kFusedMN) {
+        if (engine == kFusedMN || engine == kFusedPair) {
             const uint32_t pw = (uint32_t)std::min(64, s.n_inputs);
             const uint64_t dims[3] = {(uint64_t)s.n_inputs, (uint64_t)s.n_chan, (uint64_t)s.n_time};
             const uint64_t strides[2] = {(uint64_t)s.n_inputs, (uint64_t)s.n_inputs * s.n_chan};
@@ -761,11 +1115,17 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         d.n_chan = s.n_chan;
         d.n_time = s.n_time;
         d.accumulate = jobs[j].accumulate ? 1 : 0;
-        d.nb = g.nb;
-        d.max_strip = jobs[j].max_strip > 0 ? jobs[j].max_strip : tune.max_strip;
-        if (d.max_strip > 4) return XE_EINVAL;
-        ms_max = std::max(ms_max, d.max_strip);
-        d.strips = strips_per_channel(g.nb, d.max_strip);
+        if (engine == kFusedPair) {             // 256x256 blocks on or above the diagonal
+            d.nb = (g.nb + 1) / 2;
+            d.strips = d.nb * (d.nb + 1) / 2;
+            d.max_strip = 2;
+        } else {
+            d.nb = g.nb;
+            d.max_strip = jobs[j].max_strip > 0 ? jobs[j].max_strip : tune.max_strip;
+            if (d.max_strip > 4) return XE_EINVAL;
+            ms_max = std::max(ms_max, d.max_strip);
+            d.strips = strips_per_channel(g.nb, d.max_strip);
+        }
         d.k_tiles = g.k_tiles;
         d.item_begin = items;
         const int64_t add = (int64_t)d.strips * s.n_chan;
@@ -784,7 +1144,12 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     const int bar_bytes = 1024;
     const int avail = kSmemMax - 1024 - bar_bytes;
     const int op_slot = kBlk * kt_of(engine), pk_slot = 64 * kt_of(engine);
-    if (engine == kFusedMN) {
+    if (engine == kFusedPair) {
+        hp.slots = kPairSlots;
+        hp.n_acc = 2;
+        hp.pk_stages = 4;
+        hp.op_stages = 4;
+    } else if (engine == kFusedMN) {
         hp.pk_stages = 3;
         hp.op_stages = std::min(8, (avail - hp.pk_stages * hp.slots * pk_slot) / (hp.slots * op_slot));
     } else {
@@ -793,8 +1158,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     }
     if (hp.op_stages < 2) return XE_EINVAL;
     const int smem = 1024 + hp.op_stages * hp.slots * op_slot + hp.pk_stages * hp.slots * pk_slot + bar_bytes;
-    const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     XE_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
+    if (engine == kFusedPair) return launch_pair(hp, items, tune.n_ctas, smem, st);
+    const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     switch (engine) {
         case kUnpackedK: return launch_gemm<kUnpackedK>(hp, ctas, smem, st);
         case kUnpackedMN: return launch_gemm<kUnpackedMN>(hp, ctas, smem, st);

@@ -108,7 +108,7 @@ def test_correlate_workspace_too_small():
     assert e.value.status == xe.XE_ENOMEM
 
 
-ENGINES = [xe.XE_ENGINE_FUSED, xe.XE_ENGINE_UNPACKED, xe.XE_ENGINE_UNPACKED_K]
+ENGINES = [xe.XE_ENGINE_FUSED, xe.XE_ENGINE_UNPACKED, xe.XE_ENGINE_UNPACKED_K, xe.XE_ENGINE_FUSED_PAIR]
 
 
 @pytest.mark.parametrize("engine", ENGINES)
@@ -138,6 +138,29 @@ def test_correlate_few_ctas(engine):
     want, _ = oracle.correlate(fr)
     (got,) = X.correlate_batched([fr], tune=dict(engine=engine, max_strip=0, k_flush=0, n_ctas=3))
     assert_vis_equal(got, want)
+
+
+def test_pair_engine_tiny():
+    """CTA-pair engine on one small frame: one 256x256 block per channel (N=64)."""
+    fr = synth.uniform_frame(64, 3, 384, 12)
+    want, _ = oracle.correlate(fr)
+    (got,) = X.correlate_batched([fr], tune=dict(engine=xe.XE_ENGINE_FUSED_PAIR, max_strip=0, k_flush=0, n_ctas=0))
+    assert_vis_equal(got, want)
+
+
+def test_pair_engine_accumulate_and_drain():
+    """CTA-pair engine: off-diagonal blocks (N=384: 3 super-blocks), TMEM drains every 128 samples,
+    and accumulation onto a previous result."""
+    a = synth.signal_frame(384, 2, 640, 21)
+    b = synth.signal_frame(384, 2, 256, 22)
+    va, _ = oracle.correlate(a)
+    vb, _ = oracle.correlate(b)
+    tune = dict(engine=xe.XE_ENGINE_FUSED_PAIR, max_strip=0, k_flush=128, n_ctas=0)
+    (got,) = X.correlate_batched([a], tune=tune)
+    jobs = [(X.dev(b), got, xe.Shape(384, 2, 256), True)]
+    ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device="cuda")
+    xe.xe_correlate_batched(jobs, ws, tune)
+    assert_vis_equal(got, va + vb)
 
 
 def test_correlate_batched_uneven():
@@ -170,7 +193,8 @@ def test_correlate_pathfinder_frame_sampled():
         want, st = oracle.correlate(host, f, 1)
         assert st == oracle.OK
         assert_vis_equal(vis[f:f + 1], want)
-    for engine, ms in ((xe.XE_ENGINE_UNPACKED, 4), (xe.XE_ENGINE_UNPACKED_K, 3), (xe.XE_ENGINE_FUSED, 1)):
+    for engine, ms in ((xe.XE_ENGINE_UNPACKED, 4), (xe.XE_ENGINE_UNPACKED_K, 3), (xe.XE_ENGINE_FUSED, 1),
+                       (xe.XE_ENGINE_FUSED_PAIR, 0)):
         (alt,) = X.correlate_batched([fr], tune=dict(engine=engine, max_strip=ms, k_flush=2048, n_ctas=0))
         assert torch.equal(alt, vis), (engine, ms)
 
