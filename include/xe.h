@@ -134,7 +134,7 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
 /* ---------------------------------------------------------------- A3/A4: correlation */
 
 /* Engines of the correlation. */
-#define XE_ENGINE_AUTO 0        /* the tuned default (XE_ENGINE_FUSED) */
+#define XE_ENGINE_AUTO 0        /* the tuned default (XE_ENGINE_FUSED_PAIR) */
 #define XE_ENGINE_UNPACKED 1    /* A2 unpack to HBM (MN-major), then the tcgen05 GEMM reads it */
 #define XE_ENGINE_FUSED 2       /* the GEMM loads packed bytes and expands them in shared memory */
 #define XE_ENGINE_UNPACKED_K 3  /* A2 unpack to HBM transposed (K-major), then the GEMM */
@@ -142,8 +142,9 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
 
 typedef struct {
     int32_t engine;      /* XE_ENGINE_* */
-    int32_t max_strip;   /* 1..4: 128x128 tiles per work item along a row; <= 2 double-buffers
-                            the tensor-memory accumulator (default 4) */
+    int32_t max_strip;   /* single-CTA engines: 1..4 tiles of 128x128 per work item along a row;
+                            <= 2 double-buffers the tensor-memory accumulator (default 4). The
+                            pair engine always computes 256x256 blocks. */
     int32_t k_flush;     /* time samples accumulated in TMEM before draining to int32; multiple
                             of 128, at most 32768 (keeps every FP32 partial sum below 2^22,
                             where it is exact); 0 = default (32768) */

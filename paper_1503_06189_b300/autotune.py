@@ -1,5 +1,6 @@
-"""Autotuner for the correlation's work-item shape: the strip width (1..4 tiles of 128x128 along one
-row of the Gram matrix per work item) per (N, T-bucket), for the fused engine.
+"""Autotuner for the correlation's work-item shape per (N, T-bucket): the single-CTA fused engine's
+strip width (1..4 tiles of 128x128 along one row of the Gram matrix per work item), and whether the
+CTA-pair engine (256x256 blocks) beats it.
 
 Wider strips reuse each converted operand block across more tiles and save conversions; narrower
 strips double-buffer the tensor-memory accumulator and spread small problems over more SMs. The best
@@ -56,9 +57,11 @@ def measure(n_inputs: int, n_time: int, candidates=CANDIDATES, reps: int = 3, de
     s = xe.Shape(n_inputs, F, T)
     vis = torch.empty((F, xe.npairs(n_inputs), 2), dtype=torch.int32, device=dev)
     out = {}
-    for ms in candidates:
-        jobs = [(frame, vis, s, False, ms)]
-        tune = dict(engine=xe.XE_ENGINE_FUSED, max_strip=ms, k_flush=0, n_ctas=0)
+    for ms in list(candidates) + ["pair"]:
+        pair = ms == "pair"
+        jobs = [(frame, vis, s, False, 0 if pair else ms)]
+        tune = dict(engine=xe.XE_ENGINE_FUSED_PAIR if pair else xe.XE_ENGINE_FUSED, max_strip=0 if pair else ms,
+                    k_flush=0, n_ctas=0)
         ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device=dev)
         xe.xe_correlate_batched(jobs, ws, tune)                       # warm-up
         best = float("inf")
@@ -83,14 +86,24 @@ class Table:
             with open(path) as f:
                 self.entries = json.load(f)
 
-    def best(self, n_inputs: int, n_time: int) -> int:
+    def _entry(self, n_inputs: int, n_time: int) -> dict:
         k = key(n_inputs, n_time)
         if k not in self.entries:
             ms = measure(n_inputs, n_time)
-            win = min(ms, key=ms.get)
-            self.entries[k] = {"max_strip": int(win), "ms": {str(c): round(v, 4) for c, v in ms.items()}}
+            strips = {c: v for c, v in ms.items() if c != "pair"}
+            win = min(strips, key=strips.get)
+            self.entries[k] = {"max_strip": int(win), "pair_wins": bool(ms["pair"] < strips[win]),
+                               "ms": {str(c): round(v, 4) for c, v in ms.items()}}
             self.save()
-        return int(self.entries[k]["max_strip"])
+        return self.entries[k]
+
+    def best(self, n_inputs: int, n_time: int) -> int:
+        """Best strip width of the single-CTA fused engine for this bucket."""
+        return int(self._entry(n_inputs, n_time)["max_strip"])
+
+    def best_engine(self, n_inputs: int, n_time: int) -> int:
+        """XE_ENGINE_FUSED_PAIR if the CTA-pair engine beat every strip width, else XE_ENGINE_FUSED."""
+        return xe.XE_ENGINE_FUSED_PAIR if self._entry(n_inputs, n_time)["pair_wins"] else xe.XE_ENGINE_FUSED
 
     def save(self):
         if not self.path:

@@ -614,6 +614,10 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
 // barriers, and the even CTA's single MMA thread commits to both CTAs.
 
 constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA: A, B
+constexpr int kPairEpiWarps = 4;              // one per TMEM lane quarter (accumulator double-buffered)
+constexpr int kPairConvWarp0 = kEpiWarp0 + kPairEpiWarps;
+constexpr int kPairConvWarps = 16;            // one 16-byte conversion task per thread and block
+constexpr int kPairThreads = 32 * (kPairConvWarp0 + kPairConvWarps);
 
 __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C) {
     int j = 0;
@@ -631,12 +635,13 @@ __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &jo
     C = R + q;
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (kConvWarp0 + kConvWarps), 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     correlate_pair_kernel(const __grid_constant__ Params p) {
     constexpr int kKt = kKtMN;
     constexpr int kOpSlotBytes = kBlk * kKt;
     constexpr int kPkSlotBytes = 64 * kKt;
-    constexpr int kTasks = kKt * 4 / (32 * kConvWarps);
+    constexpr int kTasks = kKt * 4 / (32 * kPairConvWarps);
+    static_assert(kTasks * 32 * kPairConvWarps == kKt * 4, "conversion tasks divide evenly");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int op_stage_bytes = kPairSlots * kOpSlotBytes;
@@ -675,9 +680,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (kConvWarp0 + k
         for (int a = 0; a < 2; ++a) {
             dev::mbar_init(&acc_full[a], 1);
             dev::mbar_init(&acc_empty[a], 2);
-            dev::mbar_init(&epi_done[a], kEpiWarps);
+            dev::mbar_init(&epi_done[a], kPairEpiWarps);
         }
-        for (int s = 0; s < p.op_stages; ++s) dev::mbar_init(&conv_done[s], kConvWarps);
+        for (int s = 0; s < p.op_stages; ++s) dev::mbar_init(&conv_done[s], kPairConvWarps);
         dev::mbar_init(done, 1);
         *abort_flag = 0;
         dev::fence_mbar_init();
@@ -804,9 +809,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (kConvWarp0 + k
             dev::tc_commit_pair_multicast(done, 1);
             dev::mbar_wait(done, 0, p.limit_ns);
         }
-    } else if (warp < kConvWarp0) {
+    } else if (warp < kPairConvWarp0) {
         // -------------------------------------------------------------------- epilogue (both CTAs)
         using O = Order<true>;
+        constexpr int kPerQuarter = kPairEpiWarps / 4;
         const int q = warp & 3;
         const int half = (warp - kEpiWarp0) >> 2;
         const int m = q * 32 + lane;
@@ -838,9 +844,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (kConvWarp0 + k
                     for (int k = 0; k < 8; ++k) old[k] = make_int2(0, 0);
                 }
 #pragma unroll 1
-                for (; ck < n_chunks; ck += 2) {
-                    const bool more = ck + 2 < n_chunks;
-                    if (add && more) load_old(vis_f, prow, i, jb_of(ck + 2), N, i_ok, nxt);
+                for (; ck < n_chunks; ck += kPerQuarter) {
+                    const bool more = ck + kPerQuarter < n_chunks;
+                    if (add && more) load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, nxt);
                     int vr[8], vi[8];
                     combine_chunk<true>(tb + ck * 32, im_row, vr, vi);
                     store_vis(vis_f, prow, i, jb_of(ck), N, i_ok, vr, vi, old);
@@ -858,11 +864,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (kConvWarp0 + k
         }
     } else {
         // -------------------------------------------------------------------- converters (both CTAs)
-        const int ctid = threadIdx.x - 32 * kConvWarp0;
+        const int ctid = threadIdx.x - 32 * kPairConvWarp0;
         uint32_t dst0[kTasks], dst1[kTasks];
 #pragma unroll
         for (int u = 0; u < kTasks; ++u) {
-            const int r = ctid + 32 * kConvWarps * u, t = r >> 2, c = r & 3;
+            const int r = ctid + 32 * kPairConvWarps * u, t = r >> 2, c = r & 3;
             dst0[u] = t * 128 + (((2 * c) ^ (t & 7)) << 4);
             dst1[u] = t * 128 + (((2 * c + 1) ^ (t & 7)) << 4);
         }
@@ -877,7 +883,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (kConvWarp0 + k
             bool have[kTasks];
 #pragma unroll
             for (int u = 0; u < kTasks; ++u) {
-                const int r = ctid + 32 * kConvWarps * u, t = r >> 2, c = r & 3;
+                const int r = ctid + 32 * kPairConvWarps * u, t = r >> 2, c = r & 3;
                 src[u] = t * jb.pw + 16 * c;
                 have[u] = 16 * c < jb.pw;
             }
@@ -960,7 +966,7 @@ static int engine_of(int api_engine) {
 }
 
 static void resolve_tune(const xe_tune *t, xe_tune &out) {
-    out.engine = XE_ENGINE_FUSED;
+    out.engine = XE_ENGINE_FUSED_PAIR;
     out.max_strip = 4;
     out.k_flush = kDefaultKFlush;
     out.n_ctas = 0;
@@ -1035,7 +1041,7 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaSt
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(2 * sm_count() / 2, 1, 1);
-        cfg.blockDim = dim3(32 * (kConvWarp0 + kConvWarps), 1, 1);
+        cfg.blockDim = dim3(kPairThreads, 1, 1);
         cfg.dynamicSmemBytes = kSmemMax;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
@@ -1045,7 +1051,7 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaSt
     }
     int pairs = std::min(items, max_pairs[dev]);
     if (n_ctas > 0) pairs = std::max(1, std::min(pairs, n_ctas / 2));
-    correlate_pair_kernel<<<2 * pairs, 32 * (kConvWarp0 + kConvWarps), smem, st>>>(hp);
+    correlate_pair_kernel<<<2 * pairs, kPairThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
@@ -1184,7 +1190,7 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
 size_t xe_correlate_workspace_size(xe_shape s) {
     if (!valid_shape(s)) return 0;
     xe_job j{nullptr, nullptr, s, 0, 0};
-    return corr::batched_ws(&j, 1, corr::engine_of(XE_ENGINE_FUSED));
+    return corr::batched_ws(&j, 1, corr::engine_of(XE_ENGINE_FUSED_PAIR));
 }
 
 int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate, void *ws, size_t ws_bytes,

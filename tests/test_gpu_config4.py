@@ -39,12 +39,13 @@ def test_uneven_batch_autotuned(tmp_path):
         vis.append(v)
         jobs.append((fr, v, xe.Shape(N, F, T), False, table.best(N, T)))
     assert len(table.entries) >= 1 and all(1 <= e["max_strip"] <= 4 for e in table.entries.values())
-    ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs), dtype=torch.uint8, device=dev)
-    xe.xe_correlate_batched(jobs, ws)
+    tune = dict(engine=xe.XE_ENGINE_FUSED, max_strip=0, k_flush=0, n_ctas=0)   # per-job strip widths
+    ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device=dev)
+    xe.xe_correlate_batched(jobs, ws, tune)
     torch.cuda.synchronize()
     rng = np.random.default_rng(44)
     for k, ((N, F, T), fr, v) in enumerate(zip(shapes, frames, vis)):
-        # every channel: equal to the job launched alone with the default work-item shape
+        # every channel: equal to the job launched alone on the default (CTA-pair) engine
         alone = torch.full_like(v, -2)
         ws1 = torch.empty(xe.xe_correlate_workspace_size(xe.Shape(N, F, T)), dtype=torch.uint8, device=dev)
         xe.xe_correlate(fr, xe.Shape(N, F, T), alone, False, ws1)
