@@ -280,31 +280,48 @@ def run_xe(args):
     s = xe.Shape(N, F, T)
     pkts, counts = make_packets(FR, dev, seed=3000 + 100000 * rank)
     stride = pkts[0].shape[1]
-    frame = torch.empty((T, F, N), dtype=torch.uint8, device=dev)
-    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
+    # two frame buffers: frame k is assembled on `sa` while frame k-1 is correlated on `stream`
+    frames = [torch.empty((T, F, N), dtype=torch.uint8, device=dev) for _ in range(2)]
+    filled = [torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev) for _ in range(2)]
     lost = torch.zeros(F, dtype=torch.int32, device=dev)
     stats = torch.zeros(5, dtype=torch.int32, device=dev)
     vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
     out = torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev)
     ws_a = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
     ws_c = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.Stream(device=dev)
+    stream = torch.cuda.Stream(device=dev)        # correlation + normalisation
+    sa = torch.cuda.Stream(device=dev)            # assembly
+    assembled = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    step_done = torch.cuda.Event()
     n_ev = FR * max(args.steps, 1)
     ev_c0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
     ev_c1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
     launches_per_step = FR * (3 + 1) + 1          # per frame: 3 assembly kernels + 1 GEMM; + normalise
 
-    def step(ev_base=None):
-        lost.zero_()
+    def step(ev_base=None, in_graph=False):
+        # (inside a graph capture, waits on events of the previous step are implied: replays on one
+        # stream run one after the other)
+        if not in_graph:
+            sa.wait_event(step_done)              # the previous step's normalisation read `lost`
+        with torch.cuda.stream(sa):
+            lost.zero_()
         for k in range(FR):
-            xe.xe_assemble(pkts[k], counts[k], stride, k * T // 4, GROUPS_PER_STREAM, s, frame, filled, lost,
-                           stats, ws_a, stream=stream)
+            b = k % 2
+            if k >= 2 or not in_graph:
+                sa.wait_event(consumed[b])        # correlation of frame k-2 is done with buffer b
+            xe.xe_assemble(pkts[k], counts[k], stride, k * T // 4, GROUPS_PER_STREAM, s, frames[b], filled[b],
+                           lost, stats, ws_a, stream=sa)
+            assembled[b].record(sa)
+            stream.wait_event(assembled[b])
             if ev_base is not None:
                 ev_c0[ev_base + k].record(stream)
-            xe.xe_correlate(frame, s, vis, k > 0, ws_c, stream=stream)
+            xe.xe_correlate(frames[b], s, vis, k > 0, ws_c, stream=stream)
             if ev_base is not None:
                 ev_c1[ev_base + k].record(stream)
+            consumed[b].record(stream)
         xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=stream)
+        step_done.record(stream)
 
     for _ in range(args.warmup):
         step()
@@ -317,9 +334,10 @@ def run_xe(args):
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
+        sa.wait_event(e0)                          # both streams start after e0
         for k in range(args.steps):
             step(ev_base=k * FR)
-        e1.record(stream)
+        e1.record(stream)                          # the normalisation on `stream` ends every step
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
@@ -338,7 +356,9 @@ def run_xe(args):
     try:
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            step()
+            sa.wait_stream(stream)                  # fork the assembly stream into the capture
+            step(in_graph=True)
+            stream.wait_stream(sa)                  # join it back
         with torch.cuda.stream(stream):          # replay on the stream the events are recorded on
             g.replay()
         torch.cuda.synchronize(dev)

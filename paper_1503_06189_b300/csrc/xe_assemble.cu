@@ -66,7 +66,11 @@ __global__ void claim_kernel(const uint8_t *__restrict__ pkts, Geo g, uint32_t *
 }
 
 // One warp per packet (warps [0, n_pkts)) and one warp per (slot, group) (the warps after them).
-__global__ void __launch_bounds__(256) copy_kernel(const uint8_t *__restrict__ pkts, Geo g,
+// Blocks of 128 threads: small enough to run beside the correlation kernel on the same SM, so the
+// assembly of one frame can overlap the correlation of the previous one.
+constexpr int kCopyThreads = 128;
+
+__global__ void __launch_bounds__(kCopyThreads) copy_kernel(const uint8_t *__restrict__ pkts, Geo g,
                                                    const uint32_t *__restrict__ owner, uint8_t *__restrict__ frame,
                                                    uint8_t *__restrict__ filled, uint32_t *lost, uint32_t *stats) {
     const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -154,9 +158,9 @@ int xe::assemble_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stri
         XE_TRY_CUDA(cudaGetLastError());
     }
     const uint64_t warps = (uint64_t)n_pkts + (uint64_t)slots;
-    const uint64_t blocks = (warps + 7) / 8;
+    const uint64_t blocks = (warps + asmb::kCopyThreads / 32 - 1) / (asmb::kCopyThreads / 32);
     if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
-    asmb::copy_kernel<<<(unsigned)blocks, 256, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
+    asmb::copy_kernel<<<(unsigned)blocks, asmb::kCopyThreads, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
@@ -226,9 +230,9 @@ extern "C" int xe_assemble_noalloc(const uint8_t *pkts, uint32_t n_pkts, uint32_
         asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats);
         XE_TRY_CUDA(cudaGetLastError());
     }
-    const uint64_t blocks = ((uint64_t)n_pkts + (uint64_t)slots + 7) / 8;
+    const uint64_t blocks = ((uint64_t)n_pkts + (uint64_t)slots + 3) / 4;
     if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
-    asmb::copy_kernel<<<(unsigned)blocks, 256, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
+    asmb::copy_kernel<<<(unsigned)blocks, asmb::kCopyThreads, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
