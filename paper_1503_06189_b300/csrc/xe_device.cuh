@@ -282,8 +282,8 @@ __device__ __forceinline__ uint32_t nibbles_to_e5m2(uint32_t lo_nibbles) {
 // half-precision lane, (x & 0x000F) ^ 0x6408 has the bits of 1024 + (im ^ 8) = 1032 + im and
 // (x & 0x00F0) ^ 0x6480 those of 1024 + 16 (re ^ 8) = 1152 + 16 re; subtracting 1032 resp. 1152 is
 // exact and leaves im resp. 16 re, whose low bytes are zero, so their high bytes are the E5M2 codes.
-// Six logic/permute operations (the ALU pipe), one integer multiply-high (x >> 8, on the FMA pipe)
-// and four half2 subtractions for eight codes.
+// Four logic operations (the ALU pipe), three integer multiply-highs (x >> 8 and the two byte
+// compactions, on the FMA pipe) and four half2 subtractions for eight codes.
 __device__ __forceinline__ void expand4_e5m2(uint32_t x, uint32_t &wre, uint32_t &wim) {
     const uint32_t x8 = __umulhi(x, 1u << 24);
     uint32_t im02 = (x & 0x000F000Fu) ^ 0x64086408u;
@@ -295,8 +295,10 @@ __device__ __forceinline__ void expand4_e5m2(uint32_t x, uint32_t &wre, uint32_t
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(im13) : "r"(k_im));
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re02) : "r"(k_re));
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re13) : "r"(k_re));
-    wre = __byte_perm(re02, re13, 0x7351);
-    wim = __byte_perm(im02, im13, 0x7351);
+    // codes sit in bytes 1 and 3 of each word; (w02 >> 8) | w13 compacts them, and as the bytes do
+    // not overlap this is hi(w02 * 2^24) + w13: one multiply-add on the FMA pipe, not a byte permute
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(wre) : "r"(re02), "r"(1u << 24), "r"(re13));
+    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(wim) : "r"(im02), "r"(1u << 24), "r"(im13));
 }
 
 // 16 packed samples -> 32 E5M2 codes in groups of four inputs: (16 re_0..16 re_3, im_0..im_3,
