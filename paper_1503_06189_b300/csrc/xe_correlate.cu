@@ -612,10 +612,16 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
 // a CTA are the same block. Both CTAs walk the same static item sequence (item g = pair + k *
 // pairs, channel-major); converters and epilogue warps of both CTAs arrive on the even CTA's
 // barriers, and the even CTA's single MMA thread commits to both CTAs.
+// Every single-thread role (TMA producer, MMA issuer, the two forwarders) has a warp of its own:
+// lanes of one warp on different roles run their branches in turn, and a lane suspended in an
+// mbarrier wait would hold up the lane it waits for.
 
 constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA: A, B
 constexpr int kPairEpiWarps = 4;              // one per TMEM lane quarter (accumulator double-buffered)
-constexpr int kPairConvWarp0 = kEpiWarp0 + kPairEpiWarps;
+constexpr int kPairConvFwdWarp = 2;           // forwards converter completion to the even CTA
+constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
+constexpr int kPairEpiWarp0 = 4;
+constexpr int kPairConvWarp0 = kPairEpiWarp0 + kPairEpiWarps;
 constexpr int kPairConvWarps = 16;            // one 16-byte conversion task per thread and block
 constexpr int kPairThreads = 32 * (kPairConvWarp0 + kPairConvWarps);
 
@@ -740,7 +746,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             }
             for (int q = 0; q < p.pk_stages; ++q)
                 if (issued & (1u << q)) dev::mbar_wait(&pk_full[q], (issued_parity >> q) & 1u, p.limit_ns);
-        } else if (lane == 1) {
+        }
+    } else if (warp == kPairConvFwdWarp) {
+        if (lane == 0) {
             // ---------------------------------------------------------------- converter forwarder
             // once all converter warps of this CTA finished a stage: free the packed stage and tell
             // the even CTA's MMA thread (one arrival per CTA and stage)
@@ -757,7 +765,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                     if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
                 }
             }
-        } else if (lane == 2) {
+        }
+    } else if (warp == kPairEpiFwdWarp) {
+        if (lane == 0) {
             // ---------------------------------------------------------------- epilogue forwarder
             uint32_t acc = 0, acc_ph = 0;
             bool ok = true;
@@ -809,12 +819,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             dev::tc_commit_pair_multicast(done, 1);
             dev::mbar_wait(done, 0, p.limit_ns);
         }
-    } else if (warp < kPairConvWarp0) {
+    } else if (warp >= kPairEpiWarp0 && warp < kPairConvWarp0) {
         // -------------------------------------------------------------------- epilogue (both CTAs)
         using O = Order<true>;
         constexpr int kPerQuarter = kPairEpiWarps / 4;
         const int q = warp & 3;
-        const int half = (warp - kEpiWarp0) >> 2;
+        const int half = (warp - kPairEpiWarp0) >> 2;
         const int m = q * 32 + lane;
         const bool im_row = O::comp_of(m) != 0;
         uint32_t acc = 0, acc_ph = 0;
@@ -862,7 +872,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                 acc ^= 1u;
             }
         }
-    } else {
+    } else if (warp >= kPairConvWarp0) {
         // -------------------------------------------------------------------- converters (both CTAs)
         const int ctid = threadIdx.x - 32 * kPairConvWarp0;
         uint32_t dst0[kTasks], dst1[kTasks];
