@@ -189,6 +189,29 @@ size_t xe_correlate_batched_workspace_size(const xe_job *jobs, int32_t n_jobs, c
 int xe_correlate_batched(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune, void *ws,
                          size_t ws_bytes, void *stream);
 
+/*
+ * Zero-copy assembly and correlation of one frame (A1 + A2..A4 without the assembled frame;
+ * Sec. II-A.2 for the placement rules, Sec. II-B for the correlation). The result is exactly that of
+ * xe_assemble followed by xe_correlate on the assembled frame: the same vis, filled, lost and stats.
+ * The payloads are never copied into a frame: the call builds the frame's index (which packet, if
+ * any, supplies each 4-sample slot of each 8-channel group; first arrival wins, as in
+ * xe_assemble) and the correlator reads every sample straight from its packet through that index,
+ * reading lost slots as zeros. This saves the frame's write and re-read in device memory (2 bytes
+ * of traffic per packed sample).
+ *
+ *   pkts, n_pkts, pkt_stride, seq0, groups_per_stream, s, filled, lost, stats: as xe_assemble
+ *               (T % 4 == 0, F % 8 == 0; lost and stats accumulate).
+ *   vis         as xe_correlate (accumulate != 0 adds to it).
+ *   ws          workspace of xe_correlate_packets_workspace_size(s) bytes (any contents).
+ * Runs the tuned pair engine. The packet buffer must stay unchanged until the call's work on
+ * `stream` has finished. Errors: those of xe_assemble and xe_correlate.
+ */
+size_t xe_correlate_packets_workspace_size(xe_shape s);
+int xe_correlate_packets(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
+                         int32_t groups_per_stream, xe_shape s, int32_t *vis, int accumulate,
+                         uint8_t *filled, uint32_t *lost, uint32_t *stats, void *ws, size_t ws_bytes,
+                         void *stream);
+
 /* ---------------------------------------------------------------- A5: normalisation (Sec. II-C) */
 
 /*

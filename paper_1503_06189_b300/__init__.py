@@ -24,7 +24,8 @@ XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K, XE_EN
 EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",
     "xe_assemble_workspace_size", "xe_assemble", "xe_assemble_noalloc", "xe_unpack", "xe_correlate_workspace_size",
-    "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched", "xe_normalize",
+    "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched",
+    "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_normalize",
     "xe_stream_create", "xe_stream_submit", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
     "xe_stream_stats", "xe_stream_destroy",
 ]
@@ -105,6 +106,9 @@ def _load():
     L.xe_correlate_batched_workspace_size.restype = sz
     L.xe_correlate_batched_workspace_size.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune)]
     L.xe_correlate_batched.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune), vp, sz, vp]
+    L.xe_correlate_packets_workspace_size.restype = sz
+    L.xe_correlate_packets_workspace_size.argtypes = [Shape]
+    L.xe_correlate_packets.argtypes = [vp, u32, u32, u64, i32, Shape, vp, ctypes.c_int, vp, vp, vp, vp, sz, vp]
     L.xe_normalize.argtypes = [vp, Shape, u32, vp, vp, vp, vp, vp, vp]
     L.xe_stream_create.argtypes = [ctypes.POINTER(StreamCfg), ctypes.POINTER(vp)]
     L.xe_stream_submit.argtypes = [vp, i32, vp, u32]
@@ -262,6 +266,18 @@ def xe_correlate_batched(jobs, ws, tune=None, stream=None):
     arr = _jobs(jobs)
     _check(_L.xe_correlate_batched(arr, len(jobs), _tune(tune), _ptr(ws), _nbytes(ws), _stream(stream)),
            "xe_correlate_batched")
+
+
+def xe_correlate_packets_workspace_size(shape: Shape) -> int:
+    return _L.xe_correlate_packets_workspace_size(shape)
+
+
+def xe_correlate_packets(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
+                         vis, accumulate: bool, filled, lost, stats, ws, stream=None):
+    """Zero-copy assembly + correlation: the result of xe_assemble then xe_correlate, without the frame."""
+    _check(_L.xe_correlate_packets(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(vis),
+                                   1 if accumulate else 0, _ptr(filled), _ptr(lost), _ptr(stats), _ptr(ws),
+                                   _nbytes(ws), _stream(stream)), "xe_correlate_packets")
 
 
 # ----------------------------------------------------------------------------- A5

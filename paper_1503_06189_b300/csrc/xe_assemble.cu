@@ -5,10 +5,13 @@
 // Sec. II-A.3: the data section is moved with non-temporal (streaming) loads and stores.
 //
 // Three launches, all HBM-bound and independent of thread timing:
-//   1. init   owner[slot][group] = none
+//   1. init   owner[group][slot] = none (group-major: one group's slots are contiguous)
 //   2. claim  every in-window packet k does owner = min(owner, k): the first arrival wins
 //   3. copy   packet k copies its payload iff owner == k (else it is a duplicate); every slot that
 //             no packet owns is zero-filled and its 8 channels' lost counters grow by 4 samples.
+// The zero-copy path (xe_correlate_packets) runs 1 and 2 and a tally (the counts of 3 without
+// moving any payload): the owner table is then the frame's index, through which the correlator
+// reads the packets in place.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +33,9 @@ struct Geo {
 };
 
 enum Class { kOk = 0, kLate = 2, kEarly = 3, kInvalid = 4 };
+
+// Owner table entry of (time slot, channel group).
+__device__ __forceinline__ size_t oidx(const Geo &g, int slot, int grp) { return (size_t)grp * g.Q + slot; }
 
 __device__ __forceinline__ int classify(const uint8_t *pkts, const Geo &g, uint32_t k, int &slot, int &grp) {
     const uint4 h = __ldg(reinterpret_cast<const uint4 *>(pkts + (size_t)k * g.stride));
@@ -53,7 +59,7 @@ __global__ void claim_kernel(const uint8_t *__restrict__ pkts, Geo g, uint32_t *
     int cls = -1, slot = 0, grp = 0;
     if (k < g.n_pkts) {
         cls = classify(pkts, g, k, slot, grp);
-        if (cls == kOk) atomicMin(&owner[(size_t)slot * g.G + grp], k);
+        if (cls == kOk) atomicMin(&owner[oidx(g, slot, grp)], k);
     }
     const uint32_t late = __reduce_add_sync(0xffffffffu, cls == kLate);
     const uint32_t early = __reduce_add_sync(0xffffffffu, cls == kEarly);
@@ -62,6 +68,34 @@ __global__ void claim_kernel(const uint8_t *__restrict__ pkts, Geo g, uint32_t *
         if (late) atomicAdd(&stats[2], late);
         if (early) atomicAdd(&stats[3], early);
         if (inval) atomicAdd(&stats[4], inval);
+    }
+}
+
+// Tally only (the zero-copy path): one thread per packet (threads [0, n_pkts)) and one per
+// (slot, group) after them; the ok / duplicate counts are summed per warp before their atomics.
+__global__ void tally_kernel(const uint8_t *__restrict__ pkts, Geo g, const uint32_t *__restrict__ owner,
+                             uint8_t *__restrict__ filled, uint32_t *lost, uint32_t *stats) {
+    const uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    bool ok = false, dup = false;
+    if (k < g.n_pkts) {
+        int slot = 0, grp = 0;
+        if (classify(pkts, g, (uint32_t)k, slot, grp) == kOk) {
+            ok = owner[oidx(g, slot, grp)] == (uint32_t)k;
+            dup = !ok;
+        }
+    } else if (k - g.n_pkts < (uint64_t)g.Q * g.G) {
+        const uint64_t sg = k - g.n_pkts;
+        const int grp = (int)(sg % g.G);
+        const bool have = owner[oidx(g, (int)(sg / g.G), grp)] != kNone;
+        filled[sg] = have ? 1 : 0;
+        if (!have) {
+            for (int c = 0; c < 8; ++c) atomicAdd(&lost[8 * grp + c], 4u);
+        }
+    }
+    const uint32_t n_ok = __reduce_add_sync(0xffffffffu, ok), n_dup = __reduce_add_sync(0xffffffffu, dup);
+    if ((threadIdx.x & 31) == 0) {
+        if (n_ok) atomicAdd(&stats[0], n_ok);
+        if (n_dup) atomicAdd(&stats[1], n_dup);
     }
 }
 
@@ -80,7 +114,7 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const uint8_t *__res
         const uint32_t k = (uint32_t)wid;
         int slot = 0, grp = 0;
         if (classify(pkts, g, k, slot, grp) != kOk) return;
-        const bool mine = owner[(size_t)slot * g.G + grp] == k;
+        const bool mine = owner[oidx(g, slot, grp)] == k;
         if (lane == 0) atomicAdd(&stats[mine ? 0 : 1], 1u);
         if (!mine) return;
         const uint4 *src = reinterpret_cast<const uint4 *>(pkts + (size_t)k * g.stride + 16);
@@ -93,7 +127,7 @@ __global__ void __launch_bounds__(kCopyThreads) copy_kernel(const uint8_t *__res
     const uint64_t sg = wid - g.n_pkts;
     if (sg >= (uint64_t)g.Q * g.G) return;
     const int slot = (int)(sg / g.G), grp = (int)(sg % g.G);
-    const bool have = owner[sg] != kNone;
+    const bool have = owner[oidx(g, slot, grp)] != kNone;
     if (lane == 0) filled[sg] = have ? 1 : 0;
     if (have) return;
     if (lane < 8) atomicAdd(&lost[8 * grp + lane], 4u);
@@ -125,20 +159,19 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
 
 }  // extern "C"
 
-// xe_assemble for the frame of some streams: packets whose header stream id is stream_base + s map
-// to the frame's stream s (the serving loop assembles each F-engine stream into its own frame).
-int xe::assemble_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
-                         uint32_t stream_base, xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost,
-                         uint32_t *stats, void *ws, size_t ws_bytes, cudaStream_t st) {
+namespace xe {
+namespace asmb {
+
+// Checks the arguments shared by every assembly form and fills the geometry.
+static int make_geo(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                    uint32_t stream_base, const xe_shape &s, const uint8_t *filled, const uint32_t *lost,
+                    const uint32_t *stats, Geo &g) {
     if (!valid_shape(s) || s.n_time < 4 || s.n_time % 4 || s.n_chan % 8 || gps < 1 || (s.n_chan / 8) % gps)
         return XE_EINVAL;
-    if (!frame || !filled || !lost || !stats || (n_pkts && !pkts)) return XE_EINVAL;
+    if (!filled || !lost || !stats || (n_pkts && !pkts)) return XE_EINVAL;
     if (pkt_stride % 16 || pkt_stride < 16u + 32u * (uint32_t)s.n_inputs) return XE_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(pkts) | reinterpret_cast<uintptr_t>(frame)) & 15) return XE_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(lost) | reinterpret_cast<uintptr_t>(stats) | reinterpret_cast<uintptr_t>(ws)) & 3)
-        return XE_EINVAL;
-    if (!ws || ws_bytes < xe_assemble_workspace_size(s)) return XE_ENOMEM;
-    asmb::Geo g;
+    if (reinterpret_cast<uintptr_t>(pkts) & 15) return XE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(lost) | reinterpret_cast<uintptr_t>(stats)) & 3) return XE_EINVAL;
     g.stream_base = stream_base;
     g.seq0 = seq0;
     g.n_pkts = n_pkts;
@@ -149,20 +182,62 @@ int xe::assemble_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stri
     g.G = s.n_chan / 8;
     g.gps = gps;
     g.S = g.G / gps;
-    uint32_t *owner = static_cast<uint32_t *>(ws);
+    return XE_OK;
+}
+
+// init, claim and copy (kCopy) or tally (!kCopy) on stream st.
+template <bool kCopy>
+static int launch(const uint8_t *pkts, const Geo &g, uint32_t *owner, uint8_t *frame, uint8_t *filled, uint32_t *lost,
+                  uint32_t *stats, cudaStream_t st) {
     const int64_t slots = (int64_t)g.Q * g.G;
-    asmb::init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
+    init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
     XE_TRY_CUDA(cudaGetLastError());
-    if (n_pkts) {
-        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats);
+    if (g.n_pkts) {
+        claim_kernel<<<(g.n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats);
         XE_TRY_CUDA(cudaGetLastError());
     }
-    const uint64_t warps = (uint64_t)n_pkts + (uint64_t)slots;
-    const uint64_t blocks = (warps + asmb::kCopyThreads / 32 - 1) / (asmb::kCopyThreads / 32);
+    if (!kCopy) {
+        const uint64_t threads = (uint64_t)g.n_pkts + (uint64_t)slots;
+        const uint64_t blocks = (threads + 255) / 256;
+        if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
+        tally_kernel<<<(unsigned)blocks, 256, 0, st>>>(pkts, g, owner, filled, lost, stats);
+        XE_TRY_CUDA(cudaGetLastError());
+        return XE_OK;
+    }
+    const uint64_t warps = (uint64_t)g.n_pkts + (uint64_t)slots;
+    const uint64_t blocks = (warps + kCopyThreads / 32 - 1) / (kCopyThreads / 32);
     if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
-    asmb::copy_kernel<<<(unsigned)blocks, asmb::kCopyThreads, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
+    copy_kernel<<<(unsigned)blocks, kCopyThreads, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
+}
+
+}  // namespace asmb
+}  // namespace xe
+
+// xe_assemble for the frame of some streams: packets whose header stream id is stream_base + s map
+// to the frame's stream s (the serving loop assembles each F-engine stream into its own frame).
+int xe::assemble_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                         uint32_t stream_base, xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost,
+                         uint32_t *stats, void *ws, size_t ws_bytes, cudaStream_t st) {
+    asmb::Geo g;
+    if (int e = asmb::make_geo(pkts, n_pkts, pkt_stride, seq0, gps, stream_base, s, filled, lost, stats, g)) return e;
+    if (!frame || (reinterpret_cast<uintptr_t>(frame) & 15)) return XE_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) & 3) return XE_EINVAL;
+    if (!ws || ws_bytes < xe_assemble_workspace_size(s)) return XE_ENOMEM;
+    return asmb::launch<true>(pkts, g, static_cast<uint32_t *>(ws), frame, filled, lost, stats, st);
+}
+
+// The frame's index without its payload: owner[group * T/4 + slot] = the packet that supplies samples
+// 4 slot .. 4 slot + 3 of channels 8 group .. 8 group + 7, or 0xFFFFFFFF (lost: zeros); filled,
+// lost and stats exactly as xe_assemble gives them.
+int xe::index_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                      uint32_t stream_base, xe_shape s, uint8_t *filled, uint32_t *lost, uint32_t *stats,
+                      uint32_t *owner, cudaStream_t st) {
+    asmb::Geo g;
+    if (int e = asmb::make_geo(pkts, n_pkts, pkt_stride, seq0, gps, stream_base, s, filled, lost, stats, g)) return e;
+    if (!owner || (reinterpret_cast<uintptr_t>(owner) & 3)) return XE_EINVAL;
+    return asmb::launch<false>(pkts, g, owner, nullptr, filled, lost, stats, st);
 }
 
 // ---------------------------------------------------------------------------- allocation-free variant

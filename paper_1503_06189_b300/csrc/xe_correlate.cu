@@ -54,6 +54,10 @@ enum Engine { kUnpackedK = 0, kUnpackedMN = 1, kFusedMN = 2, kFusedPair = 3 };
 struct Job {                 // 128-byte aligned through its CUtensorMap
     CUtensorMap tmap;        // operand map (unpacked engines) or packed frame map (fused)
     int32_t *vis;
+    const uint8_t *frame;    // packed frame [T][F][N] (pair engine loads it directly)
+    const uint8_t *pkts;     // packet mode: packets (16-byte header, payload [4 t][8 channels][N])
+    const uint32_t *owner;   // packet mode: [F / 8][T / 4] packet of each (group, slot), ~0u = lost
+    uint32_t pkt_stride;     // packet mode: bytes from one packet to the next
     int32_t n_inputs, n_chan, n_time, accumulate;
     int32_t nb;              // 128-row operand blocks (R / 128)
     int32_t strips;          // work items per channel
@@ -612,18 +616,25 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
 // a CTA are the same block. Both CTAs walk the same static item sequence (item g = pair + k *
 // pairs, channel-major); converters and epilogue warps of both CTAs arrive on the even CTA's
 // barriers, and the even CTA's single MMA thread commits to both CTAs.
-// Every single-thread role (TMA producer, MMA issuer, the two forwarders) has a warp of its own:
-// lanes of one warp on different roles run their branches in turn, and a lane suspended in an
-// mbarrier wait would hold up the lane it waits for.
+// Shared-memory bandwidth, not the tensor pipe, bounds this design when packed tiles are staged in
+// shared memory (the MMAs alone read 32 KB of operands per stage and CTA), so the converters load
+// their packed samples from global memory straight into registers, one stage ahead, and the
+// converter forwarder keeps L2 warm with TMA prefetches a few stages further ahead; shared memory
+// then only carries the converted operands.
+// Every single-thread role (MMA issuer, the two forwarders) has a warp of its own: lanes of one
+// warp on different roles run their branches in turn, and a lane suspended in an mbarrier wait
+// would hold up the lane it waits for.
 
 constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA: A, B
 constexpr int kPairEpiWarps = 4;              // one per TMEM lane quarter (accumulator double-buffered)
-constexpr int kPairConvFwdWarp = 2;           // forwards converter completion to the even CTA
+constexpr int kPairConvFwdWarp = 2;           // forwards converter completion, prefetches into L2
 constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
 constexpr int kPairEpiWarp0 = 4;
 constexpr int kPairConvWarp0 = kPairEpiWarp0 + kPairEpiWarps;
-constexpr int kPairConvWarps = 16;            // one 16-byte conversion task per thread and block
+constexpr int kPairConvWarps = 8;             // two 16-byte conversion tasks per thread and block
 constexpr int kPairThreads = 32 * (kPairConvWarp0 + kPairConvWarps);
+constexpr int kPairMaxStages = 6;
+constexpr int kPairPrefetch = 4;              // L2 prefetch distance in stages
 
 __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C) {
     int j = 0;
@@ -641,25 +652,138 @@ __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &jo
     C = R + q;
 }
 
+// Walks the (item, k-tile) stages of one pair in order (forwarder and L2 prefetch).
+struct PairCursor {
+    int g, kt, job, f, R, C, k_tiles;
+    __device__ __forceinline__ void start(const Params &p, int g0) {
+        g = g0;
+        kt = 0;
+        if (g < p.n_items) load(p);
+    }
+    __device__ __forceinline__ void load(const Params &p) {
+        decode_pair_item(p, g, job, f, R, C);
+        k_tiles = p.jobs[job].k_tiles;
+    }
+    __device__ __forceinline__ bool valid(const Params &p) const { return g < p.n_items; }
+    __device__ __forceinline__ void next(const Params &p, int n_pairs) {
+        if (++kt < k_tiles) return;
+        kt = 0;
+        g += n_pairs;
+        if (g < p.n_items) load(p);
+    }
+};
+
+constexpr uint32_t kNoPacket = 0xFFFFFFFFu;
+
+// One converter thread's walk over the stages of its pair. The thread converts inputs 16c ..
+// 16c + 15 of the A block and (off the diagonal) of the B block, for samples t_row and t_row + 64
+// of each 128-sample k-tile; all address arithmetic of a stage is two 64-bit adds.
+// Frame mode: sample t of these bytes sits at frame + (t F + f) N + column.
+// Packet mode (the zero-copy path): sample t sits in packet o = owner[f / 8][t / 4] (the packet
+// holding time slot t / 4 of this channel's group), at pkts + o * pkt_stride + 16 + ((t % 4) 8 +
+// f % 8) N + column; a lost packet (o = ~0u) reads as zeros, as in an assembled frame. The 32
+// slots of a k-tile are looked up by one coalesced load per warp (lane l: slot l), and each thread
+// takes the packets of its two rows from lanes t_row / 4 and t_row / 4 + 16.
+template <bool kPackets>
+struct PairLoader {
+    int g, kt, k_tiles, nblk, t_left;         // t_left = T - (kt * 128 + t_row)
+    bool va, vb;                              // columns of A / B inside the frame
+    const uint8_t *pa, *pb;                   // frame: sample kt * 128 + t_row; packets: in packet 0
+    int64_t step, half;                       // frame: bytes per k-tile / per 64 samples
+    const uint32_t *own;                      // packets: owner entry of slot kt * 32 + lane
+    int s_left;                               // packets: T / 4 - (kt * 32 + lane)
+    int64_t pstride;
+
+    __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
+        int job, f, R, C;
+        decode_pair_item(p, g, job, f, R, C);
+        const Job &jb = p.jobs[job];
+        const int N = jb.n_inputs, F = jb.n_chan;
+        kt = 0;
+        k_tiles = jb.k_tiles;
+        nblk = R == C ? 1 : 2;
+        t_left = jb.n_time - t_row;
+        const int ca = (2 * R + (int)rank) * 64 + 16 * c, cb = (2 * C + (int)rank) * 64 + 16 * c;
+        va = ca < N;
+        vb = nblk == 2 && cb < N;
+        const uint8_t *base;
+        if constexpr (kPackets) {
+            const int Q = jb.n_time / 4, lane = threadIdx.x & 31;
+            base = jb.pkts + 16 + ((size_t)(t_row & 3) * 8 + f % 8) * N;
+            own = jb.owner + (size_t)(f / 8) * Q + lane;
+            s_left = Q - lane;
+            pstride = jb.pkt_stride;
+        } else {
+            base = jb.frame + ((size_t)t_row * F + f) * N;
+            step = (int64_t)kKtMN * F * N;
+            half = (int64_t)64 * F * N;
+        }
+        pa = base + ca;
+        pb = base + cb;
+    }
+    __device__ __forceinline__ void start(const Params &p, int pair, uint32_t rank, int t_row, int c) {
+        g = pair;
+        if (g < p.n_items) begin_item(p, rank, t_row, c);
+    }
+    __device__ __forceinline__ bool valid(const Params &p) const { return g < p.n_items; }
+    __device__ __forceinline__ void next(const Params &p, int n_pairs, uint32_t rank, int t_row, int c) {
+        t_left -= kKtMN;
+        if constexpr (kPackets) {
+            own += kKtMN / 4;
+            s_left -= kKtMN / 4;
+        } else {
+            pa += step;
+            pb += step;
+        }
+        if (++kt < k_tiles) return;
+        g += n_pairs;
+        if (g < p.n_items) begin_item(p, rank, t_row, c);
+    }
+    // packets: the packet of slot lane of the current stage (lane = this thread's lane)
+    __device__ __forceinline__ uint32_t owner_of_lane() const {
+        uint32_t o = kNoPacket;
+        if constexpr (kPackets) {
+            if (s_left > 0) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o) : "l"(own));
+        }
+        return o;
+    }
+    // the current stage's samples of this thread (o0, o1: its packets, packet mode)
+    __device__ __forceinline__ void load(uint32_t o0, uint32_t o1, uint4 &a0, uint4 &a1, uint4 &b0, uint4 &b1) const {
+        const uint4 z = make_uint4(0, 0, 0, 0);
+        bool r0, r1;
+        int64_t off0, off1;
+        if constexpr (kPackets) {
+            r0 = o0 != kNoPacket;
+            r1 = o1 != kNoPacket;
+            off0 = (int64_t)o0 * pstride;
+            off1 = (int64_t)o1 * pstride;
+        } else {
+            r0 = t_left > 0;
+            r1 = t_left > 64;
+            off0 = 0;
+            off1 = half;
+        }
+        a0 = r0 && va ? dev::ld_stream_16(pa + off0) : z;
+        a1 = r1 && va ? dev::ld_stream_16(pa + off1) : z;
+        b0 = r0 && vb ? dev::ld_stream_16(pb + off0) : z;
+        b1 = r1 && vb ? dev::ld_stream_16(pb + off1) : z;
+    }
+};
+
+template <bool kPackets>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     correlate_pair_kernel(const __grid_constant__ Params p) {
     constexpr int kKt = kKtMN;
     constexpr int kOpSlotBytes = kBlk * kKt;
-    constexpr int kPkSlotBytes = 64 * kKt;
-    constexpr int kTasks = kKt * 4 / (32 * kPairConvWarps);
-    static_assert(kTasks * 32 * kPairConvWarps == kKt * 4, "conversion tasks divide evenly");
+    static_assert(kKt * 4 == 2 * 32 * kPairConvWarps, "two conversion tasks per converter thread and block");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int op_stage_bytes = kPairSlots * kOpSlotBytes;
-    const int pk_stage_bytes = kPairSlots * kPkSlotBytes;
     uint8_t *op_ring = smem;
-    uint8_t *pk_ring = smem + p.op_stages * op_stage_bytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(pk_ring + p.pk_stages * pk_stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(op_ring + p.op_stages * op_stage_bytes);
     uint64_t *op_full = bars;                       // [op_stages] even CTA: both CTAs' converters
     uint64_t *op_empty = op_full + p.op_stages;     // [op_stages] pair MMAs done (multicast commit)
-    uint64_t *pk_full = op_empty + p.op_stages;     // [pk_stages] local TMA
-    uint64_t *pk_empty = pk_full + p.pk_stages;     // [pk_stages] local converters
-    uint64_t *acc_full = pk_empty + p.pk_stages;    // [2] pair MMAs of a segment done (multicast)
+    uint64_t *acc_full = op_empty + p.op_stages;    // [2] pair MMAs of a segment done (multicast)
     uint64_t *acc_empty = acc_full + 2;             // [2] even CTA: both CTAs' epilogues drained
     uint64_t *conv_done = acc_empty + 2;            // [op_stages] local: this CTA's converters finished
     uint64_t *epi_done = conv_done + p.op_stages;   // [2] local: this CTA's epilogue drained
@@ -672,27 +796,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     const bool leader = rank == 0;
     const int pair = blockIdx.x >> 1, n_pairs = gridDim.x >> 1;
     const uint32_t op_base = dev::smem_u32(op_ring);
-    const uint32_t pk_base = dev::smem_u32(pk_ring);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.op_stages; ++s) {
             dev::mbar_init(&op_full[s], 2);         // one arrival per CTA of the pair
             dev::mbar_init(&op_empty[s], 1);
-        }
-        for (int s = 0; s < p.pk_stages; ++s) {
-            dev::mbar_init(&pk_full[s], 1);
-            dev::mbar_init(&pk_empty[s], 1);
+            dev::mbar_init(&conv_done[s], kPairConvWarps);
         }
         for (int a = 0; a < 2; ++a) {
             dev::mbar_init(&acc_full[a], 1);
             dev::mbar_init(&acc_empty[a], 2);
             dev::mbar_init(&epi_done[a], kPairEpiWarps);
         }
-        for (int s = 0; s < p.op_stages; ++s) dev::mbar_init(&conv_done[s], kPairConvWarps);
         dev::mbar_init(done, 1);
         *abort_flag = 0;
         dev::fence_mbar_init();
-        for (int j = 0; j < p.n_jobs; ++j) dev::prefetch_tmap(&p.jobs[j].tmap);
+        if (!kPackets)
+            for (int j = 0; j < p.n_jobs; ++j) dev::prefetch_tmap(&p.jobs[j].tmap);
     }
     if (warp == 1) {
         dev::tmem_alloc_pair(tmem_slot, kTmemCols);
@@ -704,12 +824,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
     dev::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    auto wait = [&](uint64_t *bar, uint32_t parity, bool cluster_scope) -> bool {
-        auto test = [&] { return cluster_scope ? dev::mbar_try_wait_cluster(bar, parity) : dev::mbar_try_wait(bar, parity); };
-        if (test()) return true;
+    auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if (dev::mbar_try_wait(bar, parity)) return true;
         const uint64_t t0 = dev::globaltimer_ns();
         for (uint32_t it = 1;; ++it) {
-            if (test()) return true;
+            if (dev::mbar_try_wait(bar, parity)) return true;
             if ((it & 127u) == 0) {
                 if (*abort_flag) return false;
                 if (dev::globaltimer_ns() - t0 > p.limit_ns) {
@@ -721,48 +840,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         }
     };
 
-    if (warp == 0) {
-        if (lane == 0) {
-            // ---------------------------------------------------------------- TMA producer (both CTAs)
-            uint32_t s = 0, ph = 0, issued = 0, issued_parity = 0;
-            bool ok = true;
-            for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-                int job, f, R, C;
-                decode_pair_item(p, g, job, f, R, C);
-                const Job &jb = p.jobs[job];
-                const int nblk = R == C ? 1 : 2;
-                const uint32_t tx = nblk * jb.pw * kKt;
-                for (int kt = 0; kt < jb.k_tiles; ++kt) {
-                    if (!wait(&pk_empty[s], ph ^ 1, false)) { ok = false; break; }
-                    dev::mbar_arrive_expect_tx(&pk_full[s], tx);
-                    dev::tma_load_3d(pk_base + s * pk_stage_bytes, &jb.tmap, &pk_full[s], (2 * R + rank) * 64, f, kt * kKt);
-                    if (nblk == 2)
-                        dev::tma_load_3d(pk_base + s * pk_stage_bytes + kPkSlotBytes, &jb.tmap, &pk_full[s],
-                                         (2 * C + rank) * 64, f, kt * kKt);
-                    issued |= 1u << s;
-                    issued_parity = (issued_parity & ~(1u << s)) | (ph << s);
-                    if (++s == (uint32_t)p.pk_stages) { s = 0; ph ^= 1; }
-                }
-            }
-            for (int q = 0; q < p.pk_stages; ++q)
-                if (issued & (1u << q)) dev::mbar_wait(&pk_full[q], (issued_parity >> q) & 1u, p.limit_ns);
-        }
-    } else if (warp == kPairConvFwdWarp) {
+    if (warp == kPairConvFwdWarp) {
         if (lane == 0) {
             // ---------------------------------------------------------------- converter forwarder
-            // once all converter warps of this CTA finished a stage: free the packed stage and tell
-            // the even CTA's MMA thread (one arrival per CTA and stage)
-            uint32_t ps = 0, os = 0, oph = 0;
-            bool ok = true;
-            for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-                int job, f, R, C;
-                decode_pair_item(p, g, job, f, R, C);
-                for (int kt = 0; kt < p.jobs[job].k_tiles; ++kt) {
-                    if (!wait(&conv_done[os], oph, false)) { ok = false; break; }
-                    dev::mbar_arrive(&pk_empty[ps]);
-                    dev::mbar_arrive_remote(&op_full[os], 0);
-                    if (++ps == (uint32_t)p.pk_stages) ps = 0;
-                    if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
+            // once all converter warps of this CTA finished a stage: tell the even CTA's MMA thread
+            // (one arrival per CTA and stage), then prefetch a later stage's packed tiles into L2
+            // (frame mode: packets have no tensor map)
+            auto prefetch = [&](const PairCursor &c) {
+                if (kPackets) return;
+                const CUtensorMap *map = &p.jobs[c.job].tmap;
+                dev::tma_prefetch_l2_3d(map, (2 * c.R + (int)rank) * 64, c.f, c.kt * kKt);
+                if (c.R != c.C) dev::tma_prefetch_l2_3d(map, (2 * c.C + (int)rank) * 64, c.f, c.kt * kKt);
+            };
+            PairCursor cu, pf;
+            cu.start(p, pair);
+            pf.start(p, pair);
+            for (int k = 0; k < kPairPrefetch && pf.valid(p); ++k) {
+                prefetch(pf);
+                pf.next(p, n_pairs);
+            }
+            uint32_t os = 0, oph = 0;
+            for (; cu.valid(p); cu.next(p, n_pairs)) {
+                if (!wait(&conv_done[os], oph)) break;
+                dev::mbar_arrive_remote(&op_full[os], 0);
+                if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
+                if (pf.valid(p)) {
+                    prefetch(pf);
+                    pf.next(p, n_pairs);
                 }
             }
         }
@@ -775,7 +879,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                 int job, f, R, C;
                 decode_pair_item(p, g, job, f, R, C);
                 for (int k0 = 0; k0 < p.jobs[job].k_tiles; k0 += p.k_flush_tiles) {
-                    if (!wait(&epi_done[acc], (acc_ph >> acc) & 1u, false)) { ok = false; break; }
+                    if (!wait(&epi_done[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
                     dev::mbar_arrive_remote(&acc_empty[acc], 0);
                     acc_ph ^= 1u << acc;
                     acc ^= 1u;
@@ -795,10 +899,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                 const uint32_t b_slot = R == C ? 0u : 1u;
                 for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles) {
                     const int k1 = min(jb.k_tiles, k0 + p.k_flush_tiles);
-                    if (!wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u, false)) { ok = false; break; }
+                    if (!wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u)) { ok = false; break; }
                     dev::tc_fence_after();
                     for (int kt = k0; kt < k1; ++kt) {
-                        if (!wait(&op_full[s], ph, false)) { ok = false; break; }
+                        if (!wait(&op_full[s], ph)) { ok = false; break; }
                         dev::tc_fence_after();
                         const uint32_t sb = op_base + s * op_stage_bytes;
 #pragma unroll
@@ -841,7 +945,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             int32_t *vis_f = jb.vis + (size_t)f * (size_t)npairs(N) * 2;
             const int n_chunks = 2 * (kBlk / 32);
             for (int k0 = 0; k0 < jb.k_tiles; k0 += p.k_flush_tiles) {
-                if (!wait(&acc_full[acc], (acc_ph >> acc) & 1u, false)) { ok = false; break; }
+                if (!wait(&acc_full[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
                 dev::tc_fence_after();
                 const bool add = jb.accumulate || k0 > 0;
                 const uint32_t tb = tmem + acc * 256u + (uint32_t(q * 32) << 16);
@@ -874,61 +978,89 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
         }
     } else if (warp >= kPairConvWarp0) {
         // -------------------------------------------------------------------- converters (both CTAs)
+        // thread ctid converts inputs 16c .. 16c + 15 of samples t_row = ctid / 4 and t_row + 64 of each
+        // block: 16 packed bytes in, 32 E5M2 codes out into the two 16-byte chunks 2c and 2c + 1 of
+        // operand rows t_row and t_row + 64 (128-byte swizzle; both rows have the same phase)
         const int ctid = threadIdx.x - 32 * kPairConvWarp0;
-        uint32_t dst0[kTasks], dst1[kTasks];
-#pragma unroll
-        for (int u = 0; u < kTasks; ++u) {
-            const int r = ctid + 32 * kPairConvWarps * u, t = r >> 2, c = r & 3;
-            dst0[u] = t * 128 + (((2 * c) ^ (t & 7)) << 4);
-            dst1[u] = t * 128 + (((2 * c + 1) ^ (t & 7)) << 4);
-        }
-        uint32_t ps = 0, pph = 0, os = 0, oph = 0;
-        bool ok = true;
-        for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-            int job, f, R, C;
-            decode_pair_item(p, g, job, f, R, C);
-            const Job &jb = p.jobs[job];
-            const int nblk = R == C ? 1 : 2;
-            uint32_t src[kTasks];
-            bool have[kTasks];
-#pragma unroll
-            for (int u = 0; u < kTasks; ++u) {
-                const int r = ctid + 32 * kPairConvWarps * u, t = r >> 2, c = r & 3;
-                src[u] = t * jb.pw + 16 * c;
-                have[u] = 16 * c < jb.pw;
+        const int t_row = ctid >> 2, c = ctid & 3;
+        const uint32_t dst0 = t_row * 128 + (((2 * c) ^ (t_row & 7)) << 4);
+        const uint32_t dst1 = t_row * 128 + (((2 * c + 1) ^ (t_row & 7)) << 4);
+        constexpr uint32_t kHalfRows = 64 * 128;
+        auto convert = [&](uint32_t slot, const uint4 &v) {
+            uint4 lo, hi;
+            dev::expand16_e5m2(v, lo, hi);
+            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                         ::"r"(slot + dst0), "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w));
+            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                         ::"r"(slot + dst1), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
+        };
+        struct Buf {
+            uint4 a0, a1, b0, b1;
+            uint32_t own;                             // packet of slot `lane` of the stage it receives next
+            int nb;                                   // blocks of the stage it holds (0: none)
+        };
+        // samples of two stages ahead are in flight while a stage is converted: three buffers in
+        // rotation (the loop is unrolled three times so that none is copied); packet mode looks up
+        // a stage's packets three stages before its samples are loaded (right after the buffer that
+        // will receive them issued its previous load)
+        PairLoader<kPackets> ld, ow;
+        ld.start(p, pair, rank, t_row, c);
+        ow = ld;
+        auto next_owners = [&](Buf &b) {
+            if constexpr (kPackets) {
+                if (!ow.valid(p)) return;
+                b.own = ow.owner_of_lane();
+                ow.next(p, n_pairs, rank, t_row, c);
             }
-            for (int kt = 0; kt < jb.k_tiles; ++kt) {
-                if (!wait(&pk_full[ps], pph, false)) { ok = false; break; }
-                if (!wait(&op_empty[os], oph ^ 1, false)) { ok = false; break; }
-                const uint32_t pk = pk_base + ps * pk_stage_bytes;
-                const uint32_t op = op_base + os * op_stage_bytes;
-#pragma unroll
-                for (int b = 0; b < kPairSlots; ++b) {
-                    if (b < nblk) {
-#pragma unroll
-                        for (int u = 0; u < kTasks; ++u) {
-                            uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
-                            if (have[u]) {
-                                uint4 v;
-                                asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
-                                             : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                                             : "r"(pk + b * kPkSlotBytes + src[u]));
-                                dev::expand16_e5m2(v, lo, hi);
-                            }
-                            const uint32_t row = op + b * kOpSlotBytes;
-                            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
-                                         ::"r"(row + dst0[u]), "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w));
-                            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
-                                         ::"r"(row + dst1[u]), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
-                        }
-                    }
-                }
-                dev::fence_proxy_async_smem();                // operand visible to the tensor core
-                __syncwarp();
-                if (lane == 0) dev::mbar_arrive(&conv_done[os]);
-                if (++ps == (uint32_t)p.pk_stages) { ps = 0; pph ^= 1; }
-                if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
+        };
+        auto issue = [&](Buf &b) {
+            if (!ld.valid(p)) {
+                b.nb = 0;
+                return;
             }
+            uint32_t o0 = 0, o1 = 0;
+            if constexpr (kPackets) {
+                o0 = __shfl_sync(0xffffffffu, b.own, t_row >> 2);
+                o1 = __shfl_sync(0xffffffffu, b.own, (t_row >> 2) + 16);
+            }
+            ld.load(o0, o1, b.a0, b.a1, b.b0, b.b1);
+            b.nb = ld.nblk;
+            ld.next(p, n_pairs, rank, t_row, c);
+        };
+        uint32_t os = 0, oph = 0;
+        // load stage i + 2 into lb, look up the packets of stage i + 5 (lb's next stage), then convert
+        // stage i from cb
+        auto step = [&](Buf &lb, Buf &cb) -> bool {
+            if (cb.nb == 0) return false;
+            issue(lb);
+            next_owners(lb);
+            if (!wait(&op_empty[os], oph ^ 1)) return false;
+            const uint32_t op = op_base + os * op_stage_bytes;
+            convert(op, cb.a0);
+            convert(op + kHalfRows, cb.a1);
+            if (cb.nb == 2) {
+                convert(op + kOpSlotBytes, cb.b0);
+                convert(op + kOpSlotBytes + kHalfRows, cb.b1);
+            }
+            dev::fence_proxy_async_smem();            // operand visible to the tensor core
+            __syncwarp();
+            if (lane == 0) dev::mbar_arrive(&conv_done[os]);
+            if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
+            return true;
+        };
+        Buf x, y, z;
+        x.own = y.own = z.own = kNoPacket;
+        next_owners(x);                               // stages 0, 1, 2
+        next_owners(y);
+        next_owners(z);
+        issue(x);
+        next_owners(x);                               // stage 3
+        issue(y);
+        next_owners(y);                               // stage 4
+        for (;;) {
+            if (!step(z, x)) break;
+            if (!step(x, y)) break;
+            if (!step(y, z)) break;
         }
     }
 
@@ -997,6 +1129,15 @@ static int check_tune(const xe_tune &t) {
 
 static constexpr size_t kWsHeader = 1024;   // work-item counter; operands start 1 KiB in
 
+struct PacketSrc {
+    const uint8_t *pkts;
+    const uint32_t *owner;   // frame index [T / 4][F / 8] (xe::index_streams)
+    uint32_t pkt_stride;
+};
+
+// Packet mode needs whole 8-channel groups and whole 4-sample slots.
+static bool s_chan_misfit(const xe_shape &s) { return s.n_chan % 8 != 0 || s.n_time % 4 != 0; }
+
 static size_t batched_ws(const xe_job *jobs, int n, int engine) {
     size_t b = kWsHeader + 1024;   // + slack: the workspace is aligned up to 1 KiB inside
     for (int j = 0; j < n; ++j) b += geom(jobs[j].s, engine).y_bytes;
@@ -1037,13 +1178,15 @@ static int launch_gemm(const Params &hp, int ctas, int smem, cudaStream_t st) {
 
 // Pair engine: as many 2-CTA clusters as can be resident at once (each CTA fills an SM), one per
 // work item at most.
+template <bool kPackets>
 static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaStream_t st) {
     static int max_pairs[64] = {};
     int dev = 0;
     XE_TRY_CUDA(cudaGetDevice(&dev));
     if (dev >= 64) return XE_EINVAL;
     if (!max_pairs[dev]) {
-        XE_TRY_CUDA(cudaFuncSetAttribute(correlate_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax));
+        XE_TRY_CUDA(cudaFuncSetAttribute(correlate_pair_kernel<kPackets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemMax));
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1056,25 +1199,31 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaSt
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        XE_TRY_CUDA(cudaOccupancyMaxActiveClusters(&n, correlate_pair_kernel, &cfg));
+        XE_TRY_CUDA(cudaOccupancyMaxActiveClusters(&n, correlate_pair_kernel<kPackets>, &cfg));
         max_pairs[dev] = std::max(1, n);
     }
     int pairs = std::min(items, max_pairs[dev]);
     if (n_ctas > 0) pairs = std::max(1, std::min(pairs, n_ctas / 2));
-    correlate_pair_kernel<<<2 * pairs, kPairThreads, smem, st>>>(hp);
+    correlate_pair_kernel<kPackets><<<2 * pairs, kPairThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
 
+// pk (packet mode, pair engine only): job j reads its samples from the packets pk[j] through the
+// frame index pk[j].owner instead of from jobs[j].frame.
 static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, void *ws, size_t ws_bytes,
-                       cudaStream_t st) {
+                       cudaStream_t st, const PacketSrc *pk) {
     if (!jobs || n_jobs < 1 || n_jobs > XE_MAX_JOBS) return XE_EINVAL;
     xe_tune tune;
     resolve_tune(tune_in, tune);
     if (int e = check_tune(tune)) return e;
     const int engine = engine_of(tune.engine);
-    for (int j = 0; j < n_jobs; ++j)
-        if (int e = check_job(jobs[j].s, jobs[j].frame, jobs[j].vis)) return e;
+    if (pk && engine != kFusedPair) return XE_EINVAL;
+    for (int j = 0; j < n_jobs; ++j) {
+        const void *src = pk ? static_cast<const void *>(pk[j].pkts) : jobs[j].frame;
+        if (int e = check_job(jobs[j].s, src, jobs[j].vis)) return e;
+        if (pk && (!pk[j].owner || pk[j].pkt_stride % 16 || s_chan_misfit(jobs[j].s))) return XE_EINVAL;
+    }
     if (!ws || ws_bytes < batched_ws(jobs, n_jobs, engine)) return XE_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) & 15) return XE_EINVAL;
     int *status = status_word();
@@ -1100,7 +1249,13 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         }
         Job &d = hp.jobs[nj++];
         int enc;
-        if (engine == kFusedMN || engine == kFusedPair) {
+        if (pk) {
+            d.pkts = pk[j].pkts;
+            d.owner = pk[j].owner;
+            d.pkt_stride = pk[j].pkt_stride;
+            d.pw = 64;
+            enc = XE_OK;
+        } else if (engine == kFusedMN || engine == kFusedPair) {
             const uint32_t pw = (uint32_t)std::min(64, s.n_inputs);
             const uint64_t dims[3] = {(uint64_t)s.n_inputs, (uint64_t)s.n_chan, (uint64_t)s.n_time};
             const uint64_t strides[2] = {(uint64_t)s.n_inputs, (uint64_t)s.n_inputs * s.n_chan};
@@ -1127,6 +1282,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         }
         if (enc != XE_OK) return XE_EINVAL;
         d.vis = jobs[j].vis;
+        d.frame = static_cast<const uint8_t *>(jobs[j].frame);
         d.n_inputs = s.n_inputs;
         d.n_chan = s.n_chan;
         d.n_time = s.n_time;
@@ -1163,8 +1319,8 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     if (engine == kFusedPair) {
         hp.slots = kPairSlots;
         hp.n_acc = 2;
-        hp.pk_stages = 4;
-        hp.op_stages = 4;
+        hp.pk_stages = 0;
+        hp.op_stages = std::min(kPairMaxStages, avail / (hp.slots * op_slot));
     } else if (engine == kFusedMN) {
         hp.pk_stages = 3;
         hp.op_stages = std::min(8, (avail - hp.pk_stages * hp.slots * pk_slot) / (hp.slots * op_slot));
@@ -1175,7 +1331,8 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     if (hp.op_stages < 2) return XE_EINVAL;
     const int smem = 1024 + hp.op_stages * hp.slots * op_slot + hp.pk_stages * hp.slots * pk_slot + bar_bytes;
     XE_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
-    if (engine == kFusedPair) return launch_pair(hp, items, tune.n_ctas, smem, st);
+    if (engine == kFusedPair)
+        return pk ? launch_pair<true>(hp, items, tune.n_ctas, smem, st) : launch_pair<false>(hp, items, tune.n_ctas, smem, st);
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     switch (engine) {
         case kUnpackedK: return launch_gemm<kUnpackedK>(hp, ctas, smem, st);
@@ -1206,7 +1363,7 @@ size_t xe_correlate_workspace_size(xe_shape s) {
 int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate, void *ws, size_t ws_bytes,
                  void *stream) {
     xe_job j{frame, vis, s, accumulate ? 1 : 0, 0};
-    return corr::run_batched(&j, 1, nullptr, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+    return corr::run_batched(&j, 1, nullptr, ws, ws_bytes, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 size_t xe_correlate_batched_workspace_size(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune) {
@@ -1222,7 +1379,32 @@ size_t xe_correlate_batched_workspace_size(const xe_job *jobs, int32_t n_jobs, c
 
 int xe_correlate_batched(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune, void *ws, size_t ws_bytes,
                          void *stream) {
-    return corr::run_batched(jobs, n_jobs, tune, ws, ws_bytes, static_cast<cudaStream_t>(stream));
+    return corr::run_batched(jobs, n_jobs, tune, ws, ws_bytes, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+size_t xe_correlate_packets_workspace_size(xe_shape s) {
+    if (!valid_shape(s) || s.n_time % 4 || s.n_chan % 8) return 0;
+    xe_job j{nullptr, nullptr, s, 0, 0};
+    const size_t owner_bytes = (size_t)round_up((int64_t)(s.n_time / 4) * (s.n_chan / 8) * 4, 1024);
+    return 1024 + owner_bytes + corr::batched_ws(&j, 1, corr::engine_of(XE_ENGINE_FUSED_PAIR));
+}
+
+int xe_correlate_packets(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                         xe_shape s, int32_t *vis, int accumulate, uint8_t *filled, uint32_t *lost, uint32_t *stats,
+                         void *ws, size_t ws_bytes, void *stream) {
+    const size_t need = xe_correlate_packets_workspace_size(s);
+    if (need == 0) return XE_EINVAL;
+    if (!ws || ws_bytes < need) return XE_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
+    const size_t owner_bytes = (size_t)round_up((int64_t)(s.n_time / 4) * (s.n_chan / 8) * 4, 1024);
+    uint32_t *owner = reinterpret_cast<uint32_t *>(base);
+    if (int e = xe::index_streams(pkts, n_pkts, pkt_stride, seq0, gps, 0, s, filled, lost, stats, owner, st)) return e;
+    // an empty packet buffer still yields a (zero) integration: point the gather at a valid address
+    corr::PacketSrc src{n_pkts ? pkts : base, owner, pkt_stride};
+    xe_job j{nullptr, vis, s, accumulate ? 1 : 0, 0};
+    const size_t used = (size_t)(base - static_cast<uint8_t *>(ws)) + owner_bytes;
+    return corr::run_batched(&j, 1, nullptr, base + owner_bytes, ws_bytes - used, st, &src);
 }
 
 }  // extern "C"

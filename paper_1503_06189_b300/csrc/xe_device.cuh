@@ -128,6 +128,23 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
+// Prefetches a 3-D tile of a tensor map into L2 (no shared memory, no completion signal).
+// Out-of-range parts of the box are ignored.
+__device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap *map, int32_t c0, int32_t c1, int32_t c2) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
+// 16-byte global load through the read-only path, not kept in L1 (streamed operand data).
+__device__ __forceinline__ uint4 ld_stream_16(const uint8_t *ptr) {
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(ptr));
+    return v;
+}
+
 // ------------------------------------------------------------------ tcgen05 (TMEM + MMA)
 
 // Allocates `ncols` TMEM columns (power of two >= 32); the base address is written to smem.

@@ -47,6 +47,12 @@ int assemble_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, 
                      uint32_t stream_base, xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost,
                      uint32_t *stats, void *ws, size_t ws_bytes, cudaStream_t st);
 
+// The assembly's index without its payload copy (see xe_assemble.cu): owner[F / 8][T / 4], the
+// packet holding each (channel group, time slot), 0xFFFFFFFF where none arrived.
+int index_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps,
+                  uint32_t stream_base, xe_shape s, uint8_t *filled, uint32_t *lost, uint32_t *stats,
+                  uint32_t *owner, cudaStream_t st);
+
 inline bool valid_shape(const xe_shape &s) {
     return s.n_inputs >= 16 && s.n_inputs <= 4096 && s.n_inputs % 16 == 0 && s.n_chan >= 1 &&
            s.n_time >= 0;

@@ -3,6 +3,7 @@
     python -m paper_1503_06189_b300.prof correlate --n 256 --f 128 --t 4096 --iters 3 [--engine 1]
     python -m paper_1503_06189_b300.prof assemble  --n 256 --f 128 --t 4096 --iters 3
     python -m paper_1503_06189_b300.prof normalize --n 256 --f 128 --iters 3
+    python -m paper_1503_06189_b300.prof packets   --n 256 --f 128 --t 4096 --iters 3
 
 Inputs are uniform random bytes generated on the device; sizes default to a frame larger than L2
 (128 MiB) so that DRAM counters are meaningful, while the device footprint stays at a few GB.
@@ -20,13 +21,17 @@ import paper_1503_06189_b300 as xe
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["correlate", "assemble", "normalize"])
+    ap.add_argument("op", choices=["correlate", "assemble", "normalize", "packets"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--f", type=int, default=128)
     ap.add_argument("--t", type=int, default=4096)
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--engine", type=int, default=0)
     ap.add_argument("--max-strip", type=int, default=0)
+    ap.add_argument("--order", choices=["arrival", "group"], default="arrival",
+                    help="packets: keep arrival (sequence-major) order or sort them group-major")
+    ap.add_argument("--align", action="store_true",
+                    help="packets: re-lay the packets at a 128-byte multiple stride with 128-byte aligned payloads")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     g = torch.Generator(device=dev)
@@ -62,6 +67,51 @@ def main(argv=None):
         ws = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
         for _ in range(a.iters):
             xe.xe_assemble(pk, pk.shape[0], pk.shape[1], 0, 1, s, out, filled, lost, stats, ws)
+    elif a.op == "packets":
+        # zero-copy assembly + correlation against assembly then correlation, same packets
+        import synth
+        pk = synth.packetize_torch(frame, 0, 1)
+        del frame
+        keep = torch.rand(pk.shape[0], generator=g, device=dev) >= 0.001
+        pk = pk[keep].contiguous()
+        if a.order == "group":                                  # all slots of a group together
+            hdr = pk[:, :16].contiguous().view(torch.int32)
+            key = (hdr[:, 0] & 0xFFFF).to(torch.int64) * (1 << 32) + hdr[:, 2].to(torch.int64)
+            pk = pk[torch.argsort(key)].contiguous()
+        if a.align:
+            stride = (pk.shape[1] + 127) // 128 * 128
+            buf = torch.zeros(pk.shape[0] * stride + 128, dtype=torch.uint8, device=dev)
+            off = (112 - buf.data_ptr()) % 128                 # header at 112 mod 128: payload 128-aligned
+            view = buf[off:off + pk.shape[0] * stride].view(pk.shape[0], stride)
+            view[:, :pk.shape[1]] = pk
+            pk = view
+        filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
+        lost = torch.zeros(F, dtype=torch.int32, device=dev)
+        stats = torch.zeros(5, dtype=torch.int32, device=dev)
+        ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device=dev)
+        out = torch.empty((T, F, N), dtype=torch.uint8, device=dev)
+        wsa = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
+        wsc = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
+
+        def zero_copy():
+            xe.xe_correlate_packets(pk, pk.shape[0], pk.shape[1], 0, 1, s, vis, False, filled, lost, stats, ws)
+
+        def two_step():
+            xe.xe_assemble(pk, pk.shape[0], pk.shape[1], 0, 1, s, out, filled, lost, stats, wsa)
+            xe.xe_correlate(out, s, vis, False, wsc)
+
+        cmac = F * P * T
+        for name, fn in (("zero-copy", zero_copy), ("two-step", two_step)):
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.iters)]
+            for e0, e1 in evs:
+                e0.record()
+                fn()
+                e1.record()
+            torch.cuda.synchronize()
+            ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+            best = min(ms[1:] if len(ms) > 1 else ms)
+            print(f"packets {name} N={N} F={F} T={T}: best {best:.4f} ms, {cmac / best / 1e9:.3f} TCMAC/s",
+                  flush=True)
     else:
         lost = torch.zeros(F, dtype=torch.int32, device=dev)
         out = torch.empty((F, P, 2), dtype=torch.float32, device=dev)
