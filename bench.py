@@ -4,9 +4,10 @@
 Workload (one "step"): the full 400 MHz CHIME Pathfinder band, N = 256 inputs x F = 1024 channels,
 a stream of 64 frames of T = 4096 samples (0.671 s of sky at 390,625 samples/s per channel). Each
 frame arrives as 131,072 UDP packets (16-byte header + 8 KiB payload, 128 streams of 8 channels)
-already resident in HBM; per frame: xe_assemble (packets -> frame, loss zero-fill) then
-xe_correlate with accumulation; at the end of the integration xe_normalize. Inputs are synthetic
-(seeded noise + 3 point sources, 4+4-bit), 64 distinct frames, ~69 GB of packets: larger than L2.
+already resident in HBM; per frame one xe_correlate_packets call (the frame's index from the
+packet headers, then the correlation reading every sample from its packet, lost packets as zeros,
+accumulating); at the end of the integration xe_normalize. Inputs are synthetic (seeded noise + 3
+point sources, 4+4-bit), 64 distinct frames, ~69 GB of packets: larger than L2.
 
 Prints one JSON line (rank 0). Metric: CMAC/s (complex multiply-accumulates of the upper-triangle
 visibilities, F * N(N+1)/2 * T per frame) and the real-time factor.
@@ -233,8 +234,8 @@ def run_serving(xe, torch, dev, frames_per_stream: int = 4, seed: int = 5000):
 
 def workload_config(args):
     return {"workload": f"full band batched: N={N_INPUTS}, F={N_CHAN} channels, {args.frames} frames x "
-                        f"T={N_TIME} from 16-byte-header UDP packets (128 streams x 8 ch), assemble + "
-                        f"correlate (accumulate) per frame, normalise per integration",
+                        f"T={N_TIME} from 16-byte-header UDP packets (128 streams x 8 ch, 0.1% lost), "
+                        f"zero-copy assemble + correlate (accumulate) per frame, normalise per integration",
             "n_inputs": N_INPUTS, "n_chan": N_CHAN, "n_time": N_TIME, "frames": args.frames,
             "l2": "inputs larger than L2 (distinct packets per frame)", "parallelism": f"replica x{args.gpus}"}
 
@@ -280,48 +281,29 @@ def run_xe(args):
     s = xe.Shape(N, F, T)
     pkts, counts = make_packets(FR, dev, seed=3000 + 100000 * rank)
     stride = pkts[0].shape[1]
-    # two frame buffers: frame k is assembled on `sa` while frame k-1 is correlated on `stream`
-    frames = [torch.empty((T, F, N), dtype=torch.uint8, device=dev) for _ in range(2)]
-    filled = [torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev) for _ in range(2)]
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
     lost = torch.zeros(F, dtype=torch.int32, device=dev)
     stats = torch.zeros(5, dtype=torch.int32, device=dev)
     vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
     out = torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev)
-    ws_a = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
-    ws_c = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.Stream(device=dev)        # correlation + normalisation
-    sa = torch.cuda.Stream(device=dev)            # assembly
-    assembled = [torch.cuda.Event() for _ in range(2)]
-    consumed = [torch.cuda.Event() for _ in range(2)]
-    step_done = torch.cuda.Event()
+    ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
     n_ev = FR * max(args.steps, 1)
     ev_c0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
     ev_c1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
-    launches_per_step = FR * (3 + 1) + 1          # per frame: 3 assembly kernels + 1 GEMM; + normalise
+    launches_per_step = FR * 4 + 1                # per frame: init, claim, tally, correlation; + normalise
 
-    def step(ev_base=None, in_graph=False):
-        # (inside a graph capture, waits on events of the previous step are implied: replays on one
-        # stream run one after the other)
-        if not in_graph:
-            sa.wait_event(step_done)              # the previous step's normalisation read `lost`
-        with torch.cuda.stream(sa):
+    def step(ev_base=None):
+        with torch.cuda.stream(stream):
             lost.zero_()
         for k in range(FR):
-            b = k % 2
-            if k >= 2 or not in_graph:
-                sa.wait_event(consumed[b])        # correlation of frame k-2 is done with buffer b
-            xe.xe_assemble(pkts[k], counts[k], stride, k * T // 4, GROUPS_PER_STREAM, s, frames[b], filled[b],
-                           lost, stats, ws_a, stream=sa)
-            assembled[b].record(sa)
-            stream.wait_event(assembled[b])
             if ev_base is not None:
                 ev_c0[ev_base + k].record(stream)
-            xe.xe_correlate(frames[b], s, vis, k > 0, ws_c, stream=stream)
+            xe.xe_correlate_packets(pkts[k], counts[k], stride, k * T // 4, GROUPS_PER_STREAM, s, vis, k > 0,
+                                    filled, lost, stats, ws, stream=stream)
             if ev_base is not None:
                 ev_c1[ev_base + k].record(stream)
-            consumed[b].record(stream)
         xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=stream)
-        step_done.record(stream)
 
     for _ in range(args.warmup):
         step()
@@ -334,10 +316,9 @@ def run_xe(args):
             dist.barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        sa.wait_event(e0)                          # both streams start after e0
         for k in range(args.steps):
             step(ev_base=k * FR)
-        e1.record(stream)                          # the normalisation on `stream` ends every step
+        e1.record(stream)
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
@@ -356,9 +337,7 @@ def run_xe(args):
     try:
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=stream):
-            sa.wait_stream(stream)                  # fork the assembly stream into the capture
-            step(in_graph=True)
-            stream.wait_stream(sa)                  # join it back
+            step()
         with torch.cuda.stream(stream):          # replay on the stream the events are recorded on
             g.replay()
         torch.cuda.synchronize(dev)
@@ -404,7 +383,8 @@ def run_xe(args):
         "realtime_factor": FR * T / SAMPLE_RATE / (ms / 1e3),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "xe_correlate (fused tcgen05 GEMM), 8 int ops per CMAC",
+                     "kernel": "xe_correlate_packets per frame (index kernels + packet-mode CTA-pair tcgen05 "
+                               "correlation), 8 int ops per CMAC, timed by CUDA events around each call",
                      "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
         "gpu_launches": launches_per_step * args.steps,
         "graph_ms_per_step": graph_ms,
@@ -446,24 +426,21 @@ def run_e2e(xe, torch, dev, pkts, counts, stride, args):
     ring = [pkts[k].cpu().pin_memory() for k in range(min(4, FR))]
     rcount = [counts[k] for k in range(len(ring))]
     dbuf = [torch.empty((max(rcount), stride), dtype=torch.uint8, device=dev) for _ in range(2)]
-    frame = torch.empty((T, F, N), dtype=torch.uint8, device=dev)
     filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
     lost = torch.zeros(F, dtype=torch.int32, device=dev)
     stats = torch.zeros(5, dtype=torch.int32, device=dev)
     vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
     out = torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev)
     host_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
-    ws_a = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
-    ws_c = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
+    ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device=dev)
     comp = torch.cuda.Stream(device=dev)
     copy = torch.cuda.Stream(device=dev)
     h2d_done = [torch.cuda.Event() for _ in range(2)]
     used = [torch.cuda.Event() for _ in range(2)]
-    h2d_bytes = 0
 
     def one_step():
-        nonlocal h2d_bytes
-        lost.zero_()
+        with torch.cuda.stream(comp):
+            lost.zero_()
         for k in range(FR):
             b = k % 2
             src = ring[k % len(ring)]
@@ -472,10 +449,9 @@ def run_e2e(xe, torch, dev, pkts, counts, stride, args):
                 dbuf[b][:src.shape[0]].copy_(src, non_blocking=True)
                 h2d_done[b].record(copy)
             comp.wait_event(h2d_done[b])
-            xe.xe_assemble(dbuf[b], rcount[k % len(ring)], stride, k * T // 4, GROUPS_PER_STREAM, s, frame,
-                           filled, lost, stats, ws_a, stream=comp)
+            xe.xe_correlate_packets(dbuf[b], rcount[k % len(ring)], stride, k * T // 4, GROUPS_PER_STREAM, s,
+                                    vis, k > 0, filled, lost, stats, ws, stream=comp)
             used[b].record(comp)
-            xe.xe_correlate(frame, s, vis, k > 0, ws_c, stream=comp)
         xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=comp)
         with torch.cuda.stream(comp):
             host_out.copy_(out, non_blocking=True)
