@@ -237,7 +237,9 @@ def workload_config(args):
                         f"T={N_TIME} from 16-byte-header UDP packets (128 streams x 8 ch, 0.1% lost), "
                         f"zero-copy assemble + correlate (accumulate) per frame, normalise per integration",
             "n_inputs": N_INPUTS, "n_chan": N_CHAN, "n_time": N_TIME, "frames": args.frames,
-            "l2": "inputs larger than L2 (distinct packets per frame)", "parallelism": f"replica x{args.gpus}"}
+            "l2": "inputs larger than L2 (distinct packets per frame)",
+            "parallelism": (f"channel shards x{args.gpus}: rank r correlates channels [1024 r, 1024 r + 1024) of a "
+                            f"{1024 * args.gpus}-channel band from its own packets; no collective on the data path")}
 
 
 # ----------------------------------------------------------------------------- GPU arm
