@@ -13,6 +13,11 @@ Prints one JSON line (rank 0). Metric: CMAC/s (complex multiply-accumulates of t
 visibilities, F * N(N+1)/2 * T per frame) and the real-time factor.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xe|reference] [--frames 64]
+    python bench.py --config 1|2|4 [--impl xe|reference]   # the other workloads, frames in HBM
+
+--config 1: N=16, F=4, T=4096 uniform nibbles; 2: the per-server Pathfinder frame N=256, F=64,
+T=16384 (signal model); 4: 24 uneven jobs (N 64..2048, F 16..256, T 1024..32768) in one batched
+launch. For these the step is correlation + normalisation of frames already in HBM.
 """
 from __future__ import annotations
 
@@ -473,6 +478,173 @@ def run_e2e(xe, torch, dev, pkts, counts, stride, args):
             "realtime_factor": FR * T / SAMPLE_RATE / dt}
 
 
+# ----------------------------------------------------------------------------- configurations 1, 2, 4
+
+def config_shapes(cfg):
+    if cfg == 1:
+        return [(16, 4, 4096)]
+    if cfg == 2:
+        return [(256, 64, 16384)]
+    import synth
+    return synth.config4_shapes()
+
+
+def config_workload(cfg):
+    return {1: "tiny: N=16, F=4, T=4096, uniform 4+4-bit nibbles (seed 1); correlate + normalise",
+            2: "Pathfinder per-server frame: N=256, F=64, T=16384 (256 MiB), signal model (seed 2); "
+               "correlate + normalise",
+            4: "uneven batch: 24 jobs (seed 4), N 64..2048, F 16..256, T 1024..32768 (27.6 GiB of frames), "
+               "one batched correlation launch + per-job normalise"}[cfg]
+
+
+def config_frame_host(cfg, k, N, F, T):
+    import synth
+    if cfg == 1:
+        return synth.uniform_frame(N, F, T, 1)
+    return synth.signal_frame(N, F, T, 2 if cfg == 2 else 4000 + k)
+
+
+def run_config_reference(args):
+    """The oracle on configuration 1 or 2 in full, or on a bounded sample of configuration 4 (first
+    channel of the jobs, smallest first, until about 10 s of CPU work)."""
+    import oracle
+
+    cfg = args.config
+    shapes = config_shapes(cfg)
+    cmac, dt, done = 0, 0.0, []
+    order = sorted(range(len(shapes)), key=lambda k: shapes[k][0] ** 2 * shapes[k][2])
+    for k in order:
+        N, F, T = shapes[k]
+        chans = F if cfg != 4 else 1
+        fr = config_frame_host(cfg, k, N, chans, T)
+        reps = 0
+        while reps == 0 or (cfg == 1 and dt < 2.0):        # the tiny frame: repeat for ~2 s
+            ts = time.perf_counter()
+            v, st = oracle.correlate(fr, 0, chans)
+            n = oracle.counts_from_counters(T, [0] * chans, N)
+            oracle.normalize(v, n)
+            dt += time.perf_counter() - ts
+            cmac += chans * npairs(N) * T
+            reps += 1
+        done.append(f"{chans} ch of N={N}, T={T}" + (f" x{reps}" if reps > 1 else ""))
+        if cfg != 4 or dt >= 10.0:
+            break
+    return {"value": cmac / dt, "unit": "CMAC/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": ("full configuration: " if cfg != 4 else "bounded sample: ") + "; ".join(done)
+                      + f" ({dt:.1f} s of CPU work)", "seconds": dt}
+
+
+def run_config(args):
+    import torch
+
+    import paper_1503_06189_b300 as xe
+    import synth
+
+    cfg = args.config
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shapes = config_shapes(cfg)
+    frames, vis, outs, lost = [], [], [], []
+    for k, (N, F, T) in enumerate(shapes):
+        if cfg == 1:
+            fr = torch.from_numpy(config_frame_host(cfg, k, N, F, T)).to(dev)
+        else:
+            fr = synth.signal_frame_torch(N, F, T, 2 if cfg == 2 else 4000 + k, device=dev,
+                                          chunk=max(1, (1 << 27) // (T * N)))
+        frames.append(fr)
+        vis.append(torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev))
+        outs.append(torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev))
+        lost.append(torch.zeros(F, dtype=torch.int32, device=dev))
+    jobs = [(fr, v, xe.Shape(*sh), False) for fr, v, sh in zip(frames, vis, shapes)]
+    ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    reps = {1: 2000, 2: 20, 4: 1}[cfg]                 # launches per step: a step lasts >= ~10 ms
+    cmac_step = reps * sum(F * npairs(N) * T for N, F, T in shapes)
+    n_ev = reps * max(args.steps, 1)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
+
+    def step(base=None):
+        for r in range(reps):
+            if base is not None:
+                ev0[base + r].record(stream)
+            xe.xe_correlate_batched(jobs, ws, stream=stream)
+            if base is not None:
+                ev1[base + r].record(stream)
+            for (N, F, T), v, o, l in zip(shapes, vis, outs, lost):
+                xe.xe_normalize(v, xe.Shape(N, F, T), T, l, o, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MiB > L2, between steps
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms_total = 0.0
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+            e0.record(stream)
+            step(base=k * reps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms_total += e0.elapsed_time(e1)
+    ms = ms_total / args.steps
+    corr_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ev0, ev1))
+    clocks = clk.summary()
+
+    # end to end: frames from pinned host memory, correlate + normalise, results back
+    e2e = None
+    try:
+        hosts = [fr.cpu().pin_memory() for fr in frames]
+        host_out = [torch.empty(o.shape, dtype=torch.float32).pin_memory() for o in outs]
+        for _ in range(2):
+            t0 = time.perf_counter()
+            with torch.cuda.stream(stream):
+                for h, fr in zip(hosts, frames):
+                    fr.copy_(h, non_blocking=True)
+            step()
+            with torch.cuda.stream(stream):
+                for h, o in zip(host_out, outs):
+                    h.copy_(o, non_blocking=True)
+            stream.synchronize()
+            dt = time.perf_counter() - t0
+        e2e = {"value": cmac_step / dt, "unit": "CMAC/s", "h2d_bytes_per_step": int(sum(h.numel() for h in hosts)),
+               "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in outs)), "ms_per_step": dt * 1e3}
+        del hosts, host_out
+    except Exception as exc:
+        e2e = {"error": str(exc)}
+
+    if rank != 0:
+        return 0
+    pk, how = peaks()
+    peak_tflops = 2.0 * pk["bf16_tflops_sustained"]
+    achieved = cmac_step / reps * 8 / (corr_ms / 1e3) / 1e12
+    sky = {1: 4096, 2: 16384}.get(cfg)
+    line = {
+        "metric": METRIC, "value": cmac_step / (ms / 1e3), "unit": "CMAC/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e5m2 x e5m2 -> f32 (exact int), int32 out", "data": "synthetic",
+        "config": {"workload": config_workload(cfg), "config": cfg, "launches_per_step": reps,
+                   "l2": "256 MiB written between steps" + ("; the tiny frame itself fits in L2" if cfg == 1 else "")},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "xe_correlate_batched (CTA-pair tcgen05 correlation), 8 int ops per CMAC",
+                     "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
+        "gpu_launches": args.steps * reps * (1 + len(shapes)),
+        "clocks": clocks, "e2e": e2e,
+    }
+    if sky:
+        line["realtime_factor"] = cmac_step / (ms / 1e3) / (npairs(shapes[0][0]) * shapes[0][1] * SAMPLE_RATE)
+    base = run_config_reference(args)
+    line["cpu_baseline"] = {k: v for k, v in base.items() if k != "seconds"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -481,9 +653,25 @@ def main():
     ap.add_argument("--frames", type=int, default=N_FRAMES)
     ap.add_argument("--impl", choices=["xe", "reference"], default="xe")
     ap.add_argument("--no-serving", action="store_true", help="skip the configuration-5 serving run")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=3,
+                    help="3: the full-band integration (default); 1, 2, 4: the other workloads")
     args = ap.parse_args()
     if args.impl == "reference":
+        if args.config != 3:
+            if int(os.environ.get("RANK", "0")) != 0:
+                return 0
+            base = run_config_reference(args)
+            print(json.dumps({"impl": "reference", "metric": METRIC, "value": base["value"], "unit": "CMAC/s",
+                              "n_gpus": args.gpus, "steps": 1, "warmup": 0, "ms_per_step": base["seconds"] * 1e3,
+                              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                              "data": "synthetic", "config": {"workload": config_workload(args.config)},
+                              "cpu_baseline": {k: v for k, v in base.items() if k != "seconds"},
+                              "e2e": {"value": base["value"], "unit": "CMAC/s", "h2d_bytes_per_step": 0,
+                                      "d2h_bytes_per_step": 0}}), flush=True)
+            return 0
         return run_reference(args)
+    if args.config != 3:
+        return run_config(args)
     return run_xe(args)
 
 

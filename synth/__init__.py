@@ -225,3 +225,17 @@ def packetize_torch(frame, seq0: int, groups_per_stream: int):
     hdr[..., 2] = seq          # low 32 bits of the little-endian u64; high word stays 0
     out[:, :HEADER_BYTES] = hdr.reshape(Q * G, 4).view(torch.uint8).reshape(Q * G, HEADER_BYTES)
     return out
+
+
+def config4_shapes(seed: int = 4, n_jobs: int = 24):
+    """The uneven batch of 24 jobs: N from {64, 128, 256, 512, 1024, 2048}, F from {16, 64, 256},
+    T log-uniform in [1024, 32768] rounded to a multiple of 128 (seeded). Returns [(N, F, T)]."""
+    rng = np.random.default_rng(seed)
+    shapes = []
+    for _ in range(n_jobs):
+        N = int(rng.choice([64, 128, 256, 512, 1024, 2048]))
+        F = int(rng.choice([16, 64, 256]))
+        T = int(np.exp(rng.uniform(np.log(1024), np.log(32768))))
+        T = max(128, (T + 64) // 128 * 128)
+        shapes.append((N, F, T))
+    return shapes

@@ -14,21 +14,9 @@ from paper_1503_06189_b300 import autotune
 pytestmark = pytest.mark.gpu
 
 
-def config4_shapes(seed=4, n_jobs=24):
-    rng = np.random.default_rng(seed)
-    shapes = []
-    for _ in range(n_jobs):
-        N = int(rng.choice([64, 128, 256, 512, 1024, 2048]))
-        F = int(rng.choice([16, 64, 256]))
-        T = int(np.exp(rng.uniform(np.log(1024), np.log(32768))))
-        T = max(128, (T + 64) // 128 * 128)
-        shapes.append((N, F, T))
-    return shapes
-
-
 def test_uneven_batch_autotuned(tmp_path):
     dev = torch.device("cuda")
-    shapes = config4_shapes()
+    shapes = synth.config4_shapes()
     table = autotune.Table(str(tmp_path / "autotune.json"))
     frames, vis, jobs = [], [], []
     for k, (N, F, T) in enumerate(shapes):
