@@ -999,10 +999,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             uint32_t own;                             // packet of slot `lane` of the stage it receives next
             int nb;                                   // blocks of the stage it holds (0: none)
         };
-        // samples of two stages ahead are in flight while a stage is converted: three buffers in
-        // rotation (the loop is unrolled three times so that none is copied); packet mode looks up
-        // a stage's packets three stages before its samples are loaded (right after the buffer that
-        // will receive them issued its previous load)
+        // samples of two (frame mode) or three (packet mode, whose gathers take longer) stages ahead
+        // are in flight while a stage is converted: three or four buffers in rotation (the loop is
+        // unrolled so that no buffer is copied); packet mode looks up a stage's packets four stages
+        // before its samples are loaded (right after the buffer that will receive them issued its
+        // previous load)
         PairLoader<kPackets> ld, ow;
         ld.start(p, pair, rank, t_row, c);
         ow = ld;
@@ -1028,8 +1029,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             ld.next(p, n_pairs, rank, t_row, c);
         };
         uint32_t os = 0, oph = 0;
-        // load stage i + 2 into lb, look up the packets of stage i + 5 (lb's next stage), then convert
-        // stage i from cb
+        // load the stage the rotation assigns to lb, look up the packets of lb's next stage, then
+        // convert stage i from cb
         auto step = [&](Buf &lb, Buf &cb) -> bool {
             if (cb.nb == 0) return false;
             issue(lb);
@@ -1048,19 +1049,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
             return true;
         };
-        Buf x, y, z;
-        x.own = y.own = z.own = kNoPacket;
-        next_owners(x);                               // stages 0, 1, 2
-        next_owners(y);
-        next_owners(z);
-        issue(x);
-        next_owners(x);                               // stage 3
-        issue(y);
-        next_owners(y);                               // stage 4
-        for (;;) {
-            if (!step(z, x)) break;
-            if (!step(x, y)) break;
-            if (!step(y, z)) break;
+        Buf x, y, z, w;
+        x.own = y.own = z.own = w.own = kNoPacket;
+        if constexpr (kPackets) {
+            next_owners(x);                           // stages 0, 1, 2, 3
+            next_owners(y);
+            next_owners(z);
+            next_owners(w);
+            issue(x);
+            next_owners(x);                           // stage 4
+            issue(y);
+            next_owners(y);                           // stage 5
+            issue(z);
+            next_owners(z);                           // stage 6
+            for (;;) {
+                if (!step(w, x)) break;
+                if (!step(x, y)) break;
+                if (!step(y, z)) break;
+                if (!step(z, w)) break;
+            }
+        } else {
+            issue(x);
+            issue(y);
+            for (;;) {
+                if (!step(z, x)) break;
+                if (!step(x, y)) break;
+                if (!step(y, z)) break;
+            }
         }
     }
 

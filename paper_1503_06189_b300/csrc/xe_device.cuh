@@ -136,10 +136,10 @@ __device__ __forceinline__ void tma_prefetch_l2_3d(const CUtensorMap *map, int32
                  : "memory");
 }
 
-// 16-byte global load through the read-only path, not kept in L1 (streamed operand data).
+// 16-byte global load cached in L2 only (streamed operand data: each byte is used once per SM).
 __device__ __forceinline__ uint4 ld_stream_16(const uint8_t *ptr) {
     uint4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
         : "l"(ptr));
     return v;
