@@ -165,7 +165,7 @@ def run_reference(args):
     return 0
 
 
-def run_serving(xe, torch, dev, frames_per_stream: int = 4, seed: int = 5000):
+def run_serving(xe, torch, dev, frames_per_stream: int = 8, seed: int = 5000, ring_frames: int = 6):
     """Configuration 5: 8 F-engine streams x 128 channels (16 groups of 8), N = 256, T = 4096 per
     frame, 16-byte-header packets with 8 KiB payloads arriving as Poisson processes totalling 819.2
     Gb/s of payload (12.5 M packets/s), 0.1% dropped, 0.5% reordered (displacement 1..64), submitted
@@ -194,7 +194,7 @@ def run_serving(xe, torch, dev, frames_per_stream: int = 4, seed: int = 5000):
     torch.cuda.synchronize(dev)
     rate = 12.5e6 / S                                  # packets/s per stream
     arrive = [np.cumsum(rng.exponential(1.0 / rate, h.shape[0])) for h in host]
-    cfg = xe.StreamCfg(S, GPS, N, T, stride, 1024, 3, 16, 8, 2, 0, 500)
+    cfg = xe.StreamCfg(S, GPS, N, T, stride, 1024, ring_frames, 16, 8, 2, 0, 500)
     handle = xe.xe_stream_create(cfg)
     pos = [0] * S
     done = 0

@@ -244,10 +244,12 @@ int xe_normalize(const int32_t *vis, xe_shape s, uint32_t t_int, const uint32_t 
  * window). The host reads only the 16-byte headers: each run of packets of one frame is copied
  * directly into that frame's device packet region. A frame closes when more than reorder_window
  * packets of later frames have arrived on its stream (or at xe_stream_flush); closed frames are
- * admitted into free device slots, assembled (xe_assemble), correlated together in one batched
- * persistent launch per admission round (xe_correlate_batched), and normalised by their sample
- * counts (xe_normalize). Rounds run on a pool of CUDA streams and overlap on the device; a host
- * callback marks each frame complete. Results stay on the device until released.
+ * admitted into free device slots, indexed (the assembly's placement rules without moving the
+ * payloads, as in xe_correlate_packets), correlated together in one batched persistent launch per
+ * admission round that reads every sample from its packet region, and normalised by their sample
+ * counts (xe_normalize). A packet region is reused once that launch has read it. Rounds run on a
+ * pool of CUDA streams and overlap on the device; a host callback marks each frame complete.
+ * Results stay on the device until released.
  *
  * Frame k of a stream covers seq [k*T/4, (k+1)*T/4). All device memory is allocated by
  * xe_stream_create (within hbm_budget when it is non-zero) and freed by xe_stream_destroy.

@@ -1144,11 +1144,7 @@ static int check_tune(const xe_tune &t) {
 
 static constexpr size_t kWsHeader = 1024;   // work-item counter; operands start 1 KiB in
 
-struct PacketSrc {
-    const uint8_t *pkts;
-    const uint32_t *owner;   // frame index [T / 4][F / 8] (xe::index_streams)
-    uint32_t pkt_stride;
-};
+using PacketSrc = xe::packet_src;
 
 // Packet mode needs whole 8-channel groups and whole 4-sample slots.
 static bool s_chan_misfit(const xe_shape &s) { return s.n_chan % 8 != 0 || s.n_time % 4 != 0; }
@@ -1359,6 +1355,12 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
 }  // namespace corr
 }  // namespace xe
 
+int xe::correlate_packets_batched(const xe_job *jobs, const packet_src *src, int n_jobs, void *ws, size_t ws_bytes,
+                                  cudaStream_t st) {
+    if (!src) return XE_EINVAL;
+    return corr::run_batched(jobs, n_jobs, nullptr, ws, ws_bytes, st, src);
+}
+
 using namespace xe;
 
 extern "C" {
@@ -1416,7 +1418,7 @@ int xe_correlate_packets(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stri
     uint32_t *owner = reinterpret_cast<uint32_t *>(base);
     if (int e = xe::index_streams(pkts, n_pkts, pkt_stride, seq0, gps, 0, s, filled, lost, stats, owner, st)) return e;
     // an empty packet buffer still yields a (zero) integration: point the gather at a valid address
-    corr::PacketSrc src{n_pkts ? pkts : base, owner, pkt_stride};
+    xe::packet_src src{n_pkts ? pkts : base, owner, pkt_stride};
     xe_job j{nullptr, vis, s, accumulate ? 1 : 0, 0};
     const size_t used = (size_t)(base - static_cast<uint8_t *>(ws)) + owner_bytes;
     return corr::run_batched(&j, 1, nullptr, base + owner_bytes, ws_bytes - used, st, &src);

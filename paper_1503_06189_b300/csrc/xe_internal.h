@@ -53,6 +53,17 @@ int index_streams(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uin
                   uint32_t stream_base, xe_shape s, uint8_t *filled, uint32_t *lost, uint32_t *stats,
                   uint32_t *owner, cudaStream_t st);
 
+// Samples of one frame read in place from its packets through its index (zero-copy correlation).
+struct packet_src {
+    const uint8_t *pkts;
+    const uint32_t *owner;       // index_streams output for this frame
+    uint32_t pkt_stride;
+};
+
+// xe_correlate_batched with job j's samples read from src[j] instead of jobs[j].frame (pair engine).
+int correlate_packets_batched(const xe_job *jobs, const packet_src *src, int n_jobs, void *ws, size_t ws_bytes,
+                              cudaStream_t st);
+
 inline bool valid_shape(const xe_shape &s) {
     return s.n_inputs >= 16 && s.n_inputs <= 4096 && s.n_inputs % 16 == 0 && s.n_chan >= 1 &&
            s.n_time >= 0;

@@ -14,8 +14,10 @@
 //   admit    the scheduler thread takes up to max_batch ready frames for which frame slots are free
 //            (continuous batching: frames that become ready while earlier rounds are on the GPU join
 //            the next round as slots free up), and enqueues on one of n_cuda_streams streams:
-//            assemble each frame into its slot, ONE batched persistent correlation launch for all
-//            of them, a normalisation per frame, and a host callback.
+//            each frame's index (which packet holds each slot; the payloads stay where they
+//            landed), ONE batched persistent correlation launch reading the samples of all of them
+//            straight from their packet regions, a normalisation per frame, and a host callback.
+//            A region is reusable once that correlation has read it.
 //   complete the callback timestamps the frames (latency = close -> complete) and queues them for
 //            xe_stream_poll; xe_stream_release returns the slot.
 #include <cuda_runtime.h>
@@ -43,7 +45,7 @@ struct Region {                  // device packet region of one frame of one str
     int64_t frame = -1;          // frame using the region, -1 = never used
     uint32_t count = 0;          // packets copied in
     bool closed = false;
-    bool issued = false;         // assembly enqueued; `consumed` marks when it has read the packets
+    bool issued = false;         // correlation enqueued; `consumed` marks when it has read the packets
     cudaEvent_t copied = nullptr;
     cudaEvent_t consumed = nullptr;
 };
@@ -57,11 +59,10 @@ struct PerStream {
 };
 
 struct Slot {
-    uint8_t *frame, *filled;
-    uint32_t *lost, *stats, *n;
+    uint8_t *filled;
+    uint32_t *lost, *stats, *n, *owner;   // owner: the frame's index, [F_s / 8][T / 4]
     int32_t *vis;
     float *out;
-    void *ws_a;
 };
 
 struct Ready {
@@ -94,7 +95,7 @@ struct xe_stream {
     int Q = 0, Fs = 0;
     int64_t P = 0;
     uint32_t cap = 0;                       // packets per region
-    size_t ws_a_bytes = 0, ws_c_bytes = 0, total_bytes = 0;
+    size_t ws_c_bytes = 0, total_bytes = 0;
     void *pool = nullptr;
     std::vector<std::unique_ptr<xe::serve::PerStream>> streams;
     std::vector<xe::serve::Slot> slot_mem;
@@ -199,6 +200,8 @@ static void scheduler(xe_stream *rt) {
         void *ws = rt->ws_c[bid % rt->cs.size()];
         BatchRec *rec = new BatchRec{rt, bid, frames, slots, {}};
         std::vector<xe_job> jobs;
+        std::vector<packet_src> srcs;
+        std::vector<Region *> regs;
         int err = XE_OK;
         for (size_t i = 0; i < frames.size(); ++i) {
             const Ready &f = frames[i];
@@ -220,19 +223,23 @@ static void scheduler(xe_stream *rt) {
             rec->packets.push_back(count);
             cudaMemsetAsync(sl.lost, 0, (size_t)rt->Fs * 4, st);
             cudaMemsetAsync(sl.stats, 0, 5 * 4, st);
-            int e = assemble_streams(pk, count, c.pkt_stride, (uint64_t)f.frame * rt->Q, c.groups_per_stream,
-                                     (uint32_t)f.stream, shape, sl.frame, sl.filled, sl.lost, sl.stats, sl.ws_a,
-                                     rt->ws_a_bytes, st);
+            int e = index_streams(pk, count, c.pkt_stride, (uint64_t)f.frame * rt->Q, c.groups_per_stream,
+                                  (uint32_t)f.stream, shape, sl.filled, sl.lost, sl.stats, sl.owner, st);
             if (e) err = e;
-            if (reg) {
-                std::lock_guard<std::mutex> lk(ps.mu);
-                cudaEventRecord(reg->consumed, st);
-                reg->issued = true;
-            }
-            jobs.push_back(xe_job{sl.frame, sl.vis, shape, 0, 0});
+            regs.push_back(reg);
+            jobs.push_back(xe_job{nullptr, sl.vis, shape, 0, 0});
+            // a frame whose region was lost has no packets: the index sends every read to zeros
+            srcs.push_back(packet_src{pk ? pk : reinterpret_cast<const uint8_t *>(sl.owner), sl.owner, c.pkt_stride});
         }
-        int e = xe_correlate_batched(jobs.data(), (int32_t)jobs.size(), nullptr, ws, rt->ws_c_bytes, st);
+        int e = correlate_packets_batched(jobs.data(), srcs.data(), (int)jobs.size(), ws, rt->ws_c_bytes, st);
         if (e) err = e;
+        for (size_t i = 0; i < frames.size(); ++i) {
+            if (!regs[i]) continue;
+            PerStream &ps = *rt->streams[frames[i].stream];
+            std::lock_guard<std::mutex> lk(ps.mu);
+            cudaEventRecord(regs[i]->consumed, st);           // the correlation has read the packets
+            regs[i]->issued = true;
+        }
         for (size_t i = 0; i < frames.size(); ++i) {
             const Slot &sl = rt->slot_mem[slots[i]];
             e = xe_normalize(sl.vis, shape, (uint32_t)c.n_time, sl.lost, nullptr, nullptr, sl.out, sl.n, st);
@@ -274,16 +281,15 @@ int xe_stream_create(const xe_stream_cfg *cfg, xe_stream **out) {
     const uint64_t pkts_per_frame = (uint64_t)rt->Q * c.groups_per_stream;
     rt->cap = (uint32_t)(pkts_per_frame + pkts_per_frame / 4 + 64);   // room for duplicates
     const xe_shape shape{c.n_inputs, rt->Fs, c.n_time};
-    rt->ws_a_bytes = round_up(xe_assemble_workspace_size(shape), 256);
+    const size_t owner_bytes = (size_t)rt->Q * (rt->Fs / 8) * 4;
     xe_job probe{nullptr, nullptr, shape, 0, 0};
     rt->ws_c_bytes = round_up(xe_correlate_batched_workspace_size(&probe, 1, nullptr), 1024);
-    if (!rt->ws_a_bytes || !rt->ws_c_bytes) return XE_EINVAL;
+    if (!rt->ws_c_bytes) return XE_EINVAL;
 
     auto al = [](size_t b) { return (size_t)round_up((int64_t)b, 1024); };
     const size_t region_bytes = al((size_t)rt->cap * c.pkt_stride);
-    const size_t slot_bytes = al((size_t)c.n_time * rt->Fs * c.n_inputs) + al((size_t)rt->Q * (rt->Fs / 8)) +
-                              al((size_t)rt->Fs * 4) + al(32) + 2 * al((size_t)rt->Fs * rt->P * 8) +
-                              al((size_t)rt->Fs * rt->P * 4) + al(rt->ws_a_bytes);
+    const size_t slot_bytes = al((size_t)rt->Q * (rt->Fs / 8)) + al((size_t)rt->Fs * 4) + al(32) +
+                              2 * al((size_t)rt->Fs * rt->P * 8) + al((size_t)rt->Fs * rt->P * 4) + al(owner_bytes);
     const size_t fixed = (size_t)c.n_streams * c.ring_frames * region_bytes + (size_t)c.n_cuda_streams * al(rt->ws_c_bytes);
     int slots = c.slots;
     if (slots == 0) {
@@ -318,14 +324,13 @@ int xe_stream_create(const xe_stream_cfg *cfg, xe_stream **out) {
     }
     for (int i = 0; i < slots; ++i) {
         Slot sl;
-        sl.frame = take((size_t)c.n_time * rt->Fs * c.n_inputs);
         sl.filled = take((size_t)rt->Q * (rt->Fs / 8));
         sl.lost = reinterpret_cast<uint32_t *>(take((size_t)rt->Fs * 4));
         sl.stats = reinterpret_cast<uint32_t *>(take(32));
         sl.vis = reinterpret_cast<int32_t *>(take((size_t)rt->Fs * rt->P * 8));
         sl.out = reinterpret_cast<float *>(take((size_t)rt->Fs * rt->P * 8));
         sl.n = reinterpret_cast<uint32_t *>(take((size_t)rt->Fs * rt->P * 4));
-        sl.ws_a = take(rt->ws_a_bytes);
+        sl.owner = reinterpret_cast<uint32_t *>(take(owner_bytes));
         rt->slot_mem.push_back(sl);
         rt->free_slots.push_back(slots - 1 - i);
     }
