@@ -631,8 +631,16 @@ constexpr int kPairConvFwdWarp = 2;           // forwards converter completion, 
 constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
 constexpr int kPairEpiWarp0 = 4;
 constexpr int kPairConvWarp0 = kPairEpiWarp0 + kPairEpiWarps;
-constexpr int kPairConvWarps = 8;             // two 16-byte conversion tasks per thread and block
-constexpr int kPairThreads = 32 * (kPairConvWarp0 + kPairConvWarps);
+// Converter shape per mode: frame mode runs 16 converter warps, one sample row per thread and
+// block per stage (more warps hide the sample loads better: 0.81 against 0.88 ms per full-band
+// frame); packet mode runs 8 warps of two rows (t and t + 64), whose 128 registers per thread hold
+// three stages of gathered samples in flight (1.02 against 1.09 ms).
+template <bool kPackets>
+struct PairShape {
+    static constexpr int kRows = kPackets ? 2 : 1;
+    static constexpr int kConvWarps = 16 / kRows;
+    static constexpr int kThreads = 32 * (kPairConvWarp0 + kConvWarps);
+};
 constexpr int kPairMaxStages = 6;
 constexpr int kPairPrefetch = 4;              // L2 prefetch distance in stages
 
@@ -764,18 +772,22 @@ struct PairLoader {
             off1 = half;
         }
         a0 = r0 && va ? dev::ld_stream_16(pa + off0) : z;
-        a1 = r1 && va ? dev::ld_stream_16(pa + off1) : z;
+        if constexpr (PairShape<kPackets>::kRows == 2) a1 = r1 && va ? dev::ld_stream_16(pa + off1) : z;
+        else a1 = z;
         b0 = r0 && vb ? dev::ld_stream_16(pb + off0) : z;
-        b1 = r1 && vb ? dev::ld_stream_16(pb + off1) : z;
+        if constexpr (PairShape<kPackets>::kRows == 2) b1 = r1 && vb ? dev::ld_stream_16(pb + off1) : z;
+        else b1 = z;
     }
 };
 
 template <bool kPackets>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>::kThreads, 1)
     correlate_pair_kernel(const __grid_constant__ Params p) {
+    constexpr int kPairRows = PairShape<kPackets>::kRows;
+    constexpr int kPairConvWarps = PairShape<kPackets>::kConvWarps;
     constexpr int kKt = kKtMN;
     constexpr int kOpSlotBytes = kBlk * kKt;
-    static_assert(kKt * 4 == 2 * 32 * kPairConvWarps, "two conversion tasks per converter thread and block");
+    static_assert(kKt * 4 == kPairRows * 32 * kPairConvWarps, "conversion tasks divide evenly");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int op_stage_bytes = kPairSlots * kOpSlotBytes;
@@ -950,24 +962,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
                 const bool add = jb.accumulate || k0 > 0;
                 const uint32_t tb = tmem + acc * 256u + (uint32_t(q * 32) << 16);
                 auto jb_of = [&](int ck) { return (cb0 * kBlk + ck * 32) / 2 + (im_row ? 8 : 0); };
-                int2 old[8], nxt[8];
+                int2 old[8];
                 int ck = half;
                 if (add && ck < n_chunks) load_old(vis_f, prow, i, jb_of(ck), N, i_ok, old);
                 else {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) old[k] = make_int2(0, 0);
                 }
+                // (the old values of the next chunk are read after this chunk's store: the epilogue has
+                // slack, and a look-ahead buffer would cost the converter warps registers)
 #pragma unroll 1
                 for (; ck < n_chunks; ck += kPerQuarter) {
                     const bool more = ck + kPerQuarter < n_chunks;
-                    if (add && more) load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, nxt);
                     int vr[8], vi[8];
                     combine_chunk<true>(tb + ck * 32, im_row, vr, vi);
                     store_vis(vis_f, prow, i, jb_of(ck), N, i_ok, vr, vi, old);
-                    if (add && more) {
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) old[k] = nxt[k];
-                    }
+                    if (add && more) load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, old);
                 }
                 dev::tc_fence_before();
                 __syncwarp();
@@ -1021,8 +1031,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             }
             uint32_t o0 = 0, o1 = 0;
             if constexpr (kPackets) {
-                o0 = __shfl_sync(0xffffffffu, b.own, t_row >> 2);
-                o1 = __shfl_sync(0xffffffffu, b.own, (t_row >> 2) + 16);
+                o0 = __shfl_sync(0xffffffffu, b.own, (t_row >> 2) & 31);
+                if constexpr (kPairRows == 2) o1 = __shfl_sync(0xffffffffu, b.own, (t_row >> 2) + 16);
             }
             ld.load(o0, o1, b.a0, b.a1, b.b0, b.b1);
             b.nb = ld.nblk;
@@ -1038,10 +1048,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
             if (!wait(&op_empty[os], oph ^ 1)) return false;
             const uint32_t op = op_base + os * op_stage_bytes;
             convert(op, cb.a0);
-            convert(op + kHalfRows, cb.a1);
+            if constexpr (kPairRows == 2) convert(op + kHalfRows, cb.a1);
             if (cb.nb == 2) {
                 convert(op + kOpSlotBytes, cb.b0);
-                convert(op + kOpSlotBytes + kHalfRows, cb.b1);
+                if constexpr (kPairRows == 2) convert(op + kOpSlotBytes + kHalfRows, cb.b1);
             }
             dev::fence_proxy_async_smem();            // operand visible to the tensor core
             __syncwarp();
@@ -1205,7 +1215,7 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaSt
         attr[0].val.clusterDim.y = 1;
         attr[0].val.clusterDim.z = 1;
         cfg.gridDim = dim3(2 * sm_count() / 2, 1, 1);
-        cfg.blockDim = dim3(kPairThreads, 1, 1);
+        cfg.blockDim = dim3(PairShape<kPackets>::kThreads, 1, 1);
         cfg.dynamicSmemBytes = kSmemMax;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
@@ -1215,7 +1225,7 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaSt
     }
     int pairs = std::min(items, max_pairs[dev]);
     if (n_ctas > 0) pairs = std::max(1, std::min(pairs, n_ctas / 2));
-    correlate_pair_kernel<kPackets><<<2 * pairs, kPairThreads, smem, st>>>(hp);
+    correlate_pair_kernel<kPackets><<<2 * pairs, PairShape<kPackets>::kThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
