@@ -39,6 +39,8 @@ namespace corr {
 constexpr int kBlk = 128;                    // rows per operand block = MMA M
 constexpr int kKtMax = 128;                  // time samples per pipeline stage (K-major engine)
 constexpr int kKtMN = 128;                   // time samples per pipeline stage (MN-major engines)
+constexpr int kPairKtFrame = 256;            // time samples per pipeline stage of the pair engine:
+constexpr int kPairKtPackets = 128;          //   frame mode / packet mode
 constexpr int kTmemCols = 512;
 constexpr int kItemRing = 4;
 constexpr int kSmemMax = 232448;             // 227 KiB opt-in limit per block
@@ -61,7 +63,7 @@ struct Job {                 // 128-byte aligned through its CUtensorMap
     int32_t n_inputs, n_chan, n_time, accumulate;
     int32_t nb;              // 128-row operand blocks (R / 128)
     int32_t strips;          // work items per channel
-    int32_t k_tiles;         // ceil(T / 128)
+    int32_t k_tiles;         // ceil(T / samples per stage)
     int32_t item_begin;      // first global work-item index of this job
     int32_t pw;              // fused: bytes per packed row in shared memory (min(64, N))
     int32_t max_strip;       // tiles per work item along a row (1..4) for this job
@@ -286,7 +288,9 @@ struct Cfg {
     static constexpr int kPkSlotBytes = 64 * kKt;       // 64 inputs x kKt samples, packed
 };
 
-__host__ __device__ constexpr int kt_of(int engine) { return engine == kUnpackedK ? kKtMax : kKtMN; }
+__host__ __device__ constexpr int kt_of(int engine, bool packets = false) {
+    return engine == kUnpackedK ? kKtMax : (engine == kFusedPair ? (packets ? kPairKtPackets : kPairKtFrame) : kKtMN);
+}
 
 template <int kEngine>
 __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(const __grid_constant__ Params p) {
@@ -631,15 +635,22 @@ constexpr int kPairConvFwdWarp = 2;           // forwards converter completion, 
 constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
 constexpr int kPairEpiWarp0 = 4;
 constexpr int kPairConvWarp0 = kPairEpiWarp0 + kPairEpiWarps;
-// Converter shape per mode: frame mode runs 16 converter warps, one sample row per thread and
-// block per stage (more warps hide the sample loads better: 0.81 against 0.88 ms per full-band
-// frame); packet mode runs 8 warps of two rows (t and t + 64), whose 128 registers per thread hold
-// three stages of gathered samples in flight (1.02 against 1.09 ms).
+// Converter shape per mode. A stage is kKt samples. Frame mode: 256-sample stages (half the
+// per-stage bookkeeping of 128: 0.80 against 0.81 ms per full-band frame), 16 converter warps (more
+// warps hide the sample loads: 0.81 against 0.88 ms), two rows per thread, three register buffers
+// (two stages in flight). Packet mode: 128-sample stages and 8 warps of two rows, whose 128
+// registers per thread hold four buffers — the gathers need three stages in flight (1.02 ms;
+// 256-sample stages spill there: 1.39 ms). kRows sample rows per thread and block, kRowStep apart.
 template <bool kPackets>
 struct PairShape {
-    static constexpr int kRows = kPackets ? 2 : 1;
-    static constexpr int kConvWarps = 16 / kRows;
+    static constexpr int kKt = kPackets ? kPairKtPackets : kPairKtFrame;
+    static constexpr int kConvWarps = kPackets ? 8 : 16;
+    static constexpr int kRows = kKt * 4 / (32 * kConvWarps);
+    static constexpr int kRowStep = kKt / kRows;
+    static constexpr int kBufs = kPackets ? 4 : 3;
     static constexpr int kThreads = 32 * (kPairConvWarp0 + kConvWarps);
+    static_assert(kRows * 32 * kConvWarps == kKt * 4, "conversion tasks divide evenly");
+    static_assert(kRowStep % 8 == 0, "a thread's rows share their 128-byte swizzle phase");
 };
 constexpr int kPairMaxStages = 6;
 constexpr int kPairPrefetch = 4;              // L2 prefetch distance in stages
@@ -684,22 +695,24 @@ struct PairCursor {
 constexpr uint32_t kNoPacket = 0xFFFFFFFFu;
 
 // One converter thread's walk over the stages of its pair. The thread converts inputs 16c ..
-// 16c + 15 of the A block and (off the diagonal) of the B block, for samples t_row and t_row + 64
-// of each 128-sample k-tile; all address arithmetic of a stage is two 64-bit adds.
+// 16c + 15 of the A block and (off the diagonal) of the B block, for samples t_row + r kRowStep
+// (r < kRows) of each kKt-sample stage; a stage's address arithmetic is two 64-bit adds.
 // Frame mode: sample t of these bytes sits at frame + (t F + f) N + column.
 // Packet mode (the zero-copy path): sample t sits in packet o = owner[f / 8][t / 4] (the packet
 // holding time slot t / 4 of this channel's group), at pkts + o * pkt_stride + 16 + ((t % 4) 8 +
-// f % 8) N + column; a lost packet (o = ~0u) reads as zeros, as in an assembled frame. The 32
-// slots of a k-tile are looked up by one coalesced load per warp (lane l: slot l), and each thread
-// takes the packets of its two rows from lanes t_row / 4 and t_row / 4 + 16.
+// f % 8) N + column; a lost packet (o = ~0u) reads as zeros, as in an assembled frame. The
+// kKt / 4 slots of a stage are looked up by coalesced loads, one per 32 slots and warp (lane l:
+// slots l, l + 32, ...), and each thread takes the packets of its rows from those lanes by shfl.
 template <bool kPackets>
 struct PairLoader {
-    int g, kt, k_tiles, nblk, t_left;         // t_left = T - (kt * 128 + t_row)
+    using S = PairShape<kPackets>;
+    static constexpr int kOwn = S::kKt / 4 / 32;          // owner loads per lane and stage
+    int g, kt, k_tiles, nblk, t_left;         // t_left = T - (kt * S::kKt + t_row)
     bool va, vb;                              // columns of A / B inside the frame
-    const uint8_t *pa, *pb;                   // frame: sample kt * 128 + t_row; packets: in packet 0
-    int64_t step, half;                       // frame: bytes per k-tile / per 64 samples
-    const uint32_t *own;                      // packets: owner entry of slot kt * 32 + lane
-    int s_left;                               // packets: T / 4 - (kt * 32 + lane)
+    const uint8_t *pa, *pb;                   // frame: sample kt * S::kKt + t_row; packets: in packet 0
+    int64_t step, rstep;                      // frame: bytes per stage / between a thread's rows
+    const uint32_t *own;                      // packets: owner entry of slot kt * S::kKt / 4 + lane
+    int s_left;                               // packets: T / 4 - (kt * S::kKt / 4 + lane)
     int64_t pstride;
 
     __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
@@ -723,8 +736,8 @@ struct PairLoader {
             pstride = jb.pkt_stride;
         } else {
             base = jb.frame + ((size_t)t_row * F + f) * N;
-            step = (int64_t)kKtMN * F * N;
-            half = (int64_t)64 * F * N;
+            step = (int64_t)S::kKt * F * N;
+            rstep = (int64_t)S::kRowStep * F * N;
         }
         pa = base + ca;
         pb = base + cb;
@@ -735,10 +748,10 @@ struct PairLoader {
     }
     __device__ __forceinline__ bool valid(const Params &p) const { return g < p.n_items; }
     __device__ __forceinline__ void next(const Params &p, int n_pairs, uint32_t rank, int t_row, int c) {
-        t_left -= kKtMN;
+        t_left -= S::kKt;
         if constexpr (kPackets) {
-            own += kKtMN / 4;
-            s_left -= kKtMN / 4;
+            own += S::kKt / 4;
+            s_left -= S::kKt / 4;
         } else {
             pa += step;
             pb += step;
@@ -747,47 +760,43 @@ struct PairLoader {
         g += n_pairs;
         if (g < p.n_items) begin_item(p, rank, t_row, c);
     }
-    // packets: the packet of slot lane of the current stage (lane = this thread's lane)
-    __device__ __forceinline__ uint32_t owner_of_lane() const {
-        uint32_t o = kNoPacket;
-        if constexpr (kPackets) {
-            if (s_left > 0) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o) : "l"(own));
+    // packets: the packets of slots lane, lane + 32, ... of the current stage
+    __device__ __forceinline__ void owners(uint32_t (&o)[kOwn > 0 ? kOwn : 1]) const {
+#pragma unroll
+        for (int q = 0; q < kOwn; ++q) {
+            o[q] = kNoPacket;
+            if constexpr (kPackets) {
+                if (s_left > 32 * q) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[q]) : "l"(own + 32 * q));
+            }
         }
-        return o;
     }
-    // the current stage's samples of this thread (o0, o1: its packets, packet mode)
-    __device__ __forceinline__ void load(uint32_t o0, uint32_t o1, uint4 &a0, uint4 &a1, uint4 &b0, uint4 &b1) const {
+    // the current stage's samples of this thread (o[r]: the packet of row r, packet mode)
+    __device__ __forceinline__ void load(const uint32_t (&o)[S::kRows], uint4 (&a)[S::kRows], uint4 (&b)[S::kRows]) const {
         const uint4 z = make_uint4(0, 0, 0, 0);
-        bool r0, r1;
-        int64_t off0, off1;
-        if constexpr (kPackets) {
-            r0 = o0 != kNoPacket;
-            r1 = o1 != kNoPacket;
-            off0 = (int64_t)o0 * pstride;
-            off1 = (int64_t)o1 * pstride;
-        } else {
-            r0 = t_left > 0;
-            r1 = t_left > 64;
-            off0 = 0;
-            off1 = half;
+#pragma unroll
+        for (int r = 0; r < S::kRows; ++r) {
+            bool ok;
+            int64_t off;
+            if constexpr (kPackets) {
+                ok = o[r] != kNoPacket;
+                off = (int64_t)o[r] * pstride;
+            } else {
+                ok = t_left > r * S::kRowStep;
+                off = r * rstep;
+            }
+            a[r] = ok && va ? dev::ld_stream_16(pa + off) : z;
+            b[r] = ok && vb ? dev::ld_stream_16(pb + off) : z;
         }
-        a0 = r0 && va ? dev::ld_stream_16(pa + off0) : z;
-        if constexpr (PairShape<kPackets>::kRows == 2) a1 = r1 && va ? dev::ld_stream_16(pa + off1) : z;
-        else a1 = z;
-        b0 = r0 && vb ? dev::ld_stream_16(pb + off0) : z;
-        if constexpr (PairShape<kPackets>::kRows == 2) b1 = r1 && vb ? dev::ld_stream_16(pb + off1) : z;
-        else b1 = z;
     }
 };
 
 template <bool kPackets>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>::kThreads, 1)
     correlate_pair_kernel(const __grid_constant__ Params p) {
-    constexpr int kPairRows = PairShape<kPackets>::kRows;
-    constexpr int kPairConvWarps = PairShape<kPackets>::kConvWarps;
-    constexpr int kKt = kKtMN;
+    using S = PairShape<kPackets>;
+    constexpr int kPairConvWarps = S::kConvWarps;
+    constexpr int kKt = S::kKt;
     constexpr int kOpSlotBytes = kBlk * kKt;
-    static_assert(kKt * 4 == kPairRows * 32 * kPairConvWarps, "conversion tasks divide evenly");
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int op_stage_bytes = kPairSlots * kOpSlotBytes;
@@ -891,7 +900,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 int job, f, R, C;
                 decode_pair_item(p, g, job, f, R, C);
                 for (int k0 = 0; k0 < p.jobs[job].k_tiles; k0 += p.k_flush_tiles) {
-                    if (!wait(&epi_done[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
+                    if (*abort_flag || !wait(&epi_done[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
                     dev::mbar_arrive_remote(&acc_empty[acc], 0);
                     acc_ph ^= 1u << acc;
                     acc ^= 1u;
@@ -911,7 +920,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 const uint32_t b_slot = R == C ? 0u : 1u;
                 for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles) {
                     const int k1 = min(jb.k_tiles, k0 + p.k_flush_tiles);
-                    if (!wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u)) { ok = false; break; }
+                    if (*abort_flag || !wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u)) { ok = false; break; }
                     dev::tc_fence_after();
                     for (int kt = k0; kt < k1; ++kt) {
                         if (!wait(&op_full[s], ph)) { ok = false; break; }
@@ -957,7 +966,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             int32_t *vis_f = jb.vis + (size_t)f * (size_t)npairs(N) * 2;
             const int n_chunks = 2 * (kBlk / 32);
             for (int k0 = 0; k0 < jb.k_tiles; k0 += p.k_flush_tiles) {
-                if (!wait(&acc_full[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
+                if (*abort_flag || !wait(&acc_full[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
                 dev::tc_fence_after();
                 const bool add = jb.accumulate || k0 > 0;
                 const uint32_t tb = tmem + acc * 256u + (uint32_t(q * 32) << 16);
@@ -988,14 +997,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         }
     } else if (warp >= kPairConvWarp0) {
         // -------------------------------------------------------------------- converters (both CTAs)
-        // thread ctid converts inputs 16c .. 16c + 15 of samples t_row = ctid / 4 and t_row + 64 of each
-        // block: 16 packed bytes in, 32 E5M2 codes out into the two 16-byte chunks 2c and 2c + 1 of
-        // operand rows t_row and t_row + 64 (128-byte swizzle; both rows have the same phase)
+        // thread ctid converts inputs 16c .. 16c + 15 of samples t_row + r kRowStep (t_row = ctid / 4)
+        // of each block: 16 packed bytes in, 32 E5M2 codes out into the two 16-byte chunks 2c and
+        // 2c + 1 of those operand rows (128-byte swizzle; all of a thread's rows share its phase)
         const int ctid = threadIdx.x - 32 * kPairConvWarp0;
         const int t_row = ctid >> 2, c = ctid & 3;
         const uint32_t dst0 = t_row * 128 + (((2 * c) ^ (t_row & 7)) << 4);
         const uint32_t dst1 = t_row * 128 + (((2 * c + 1) ^ (t_row & 7)) << 4);
-        constexpr uint32_t kHalfRows = 64 * 128;
+        constexpr uint32_t kRowBytes = S::kRowStep * 128;
         auto convert = [&](uint32_t slot, const uint4 &v) {
             uint4 lo, hi;
             dev::expand16_e5m2(v, lo, hi);
@@ -1004,23 +1013,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
                          ::"r"(slot + dst1), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
         };
+        constexpr int kOwn = PairLoader<kPackets>::kOwn > 0 ? PairLoader<kPackets>::kOwn : 1;
         struct Buf {
-            uint4 a0, a1, b0, b1;
-            uint32_t own;                             // packet of slot `lane` of the stage it receives next
+            uint4 a[S::kRows], b[S::kRows];
+            uint32_t own[kOwn];                       // packets of the stage this buffer receives next
             int nb;                                   // blocks of the stage it holds (0: none)
         };
-        // samples of two (frame mode) or three (packet mode, whose gathers take longer) stages ahead
-        // are in flight while a stage is converted: three or four buffers in rotation (the loop is
-        // unrolled so that no buffer is copied); packet mode looks up a stage's packets four stages
-        // before its samples are loaded (right after the buffer that will receive them issued its
-        // previous load)
+        // samples of kBufs - 1 stages ahead are in flight while a stage is converted: kBufs buffers
+        // in rotation (the loop is unrolled so that no buffer is copied); packet mode looks up a
+        // stage's packets kBufs stages before its samples are loaded (right after the buffer that
+        // will receive them issued its previous load)
         PairLoader<kPackets> ld, ow;
         ld.start(p, pair, rank, t_row, c);
         ow = ld;
         auto next_owners = [&](Buf &b) {
             if constexpr (kPackets) {
                 if (!ow.valid(p)) return;
-                b.own = ow.owner_of_lane();
+                ow.owners(b.own);
                 ow.next(p, n_pairs, rank, t_row, c);
             }
         };
@@ -1029,12 +1038,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 b.nb = 0;
                 return;
             }
-            uint32_t o0 = 0, o1 = 0;
-            if constexpr (kPackets) {
-                o0 = __shfl_sync(0xffffffffu, b.own, (t_row >> 2) & 31);
-                if constexpr (kPairRows == 2) o1 = __shfl_sync(0xffffffffu, b.own, (t_row >> 2) + 16);
+            uint32_t o[S::kRows];
+#pragma unroll
+            for (int r = 0; r < S::kRows; ++r) {
+                o[r] = 0;
+                if constexpr (kPackets) {
+                    // slot (r kRowStep + t_row) / 4 of the stage: register (r kRowStep / 4) / 32,
+                    // lane (r kRowStep / 4) % 32 + t_row / 4 (t_row / 4 < kRowStep / 4 <= 32)
+                    const int s0 = r * (S::kRowStep / 4);
+                    o[r] = __shfl_sync(0xffffffffu, b.own[s0 / 32], s0 % 32 + (t_row >> 2));
+                }
             }
-            ld.load(o0, o1, b.a0, b.a1, b.b0, b.b1);
+            ld.load(o, b.a, b.b);
             b.nb = ld.nblk;
             ld.next(p, n_pairs, rank, t_row, c);
         };
@@ -1047,11 +1062,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             next_owners(lb);
             if (!wait(&op_empty[os], oph ^ 1)) return false;
             const uint32_t op = op_base + os * op_stage_bytes;
-            convert(op, cb.a0);
-            if constexpr (kPairRows == 2) convert(op + kHalfRows, cb.a1);
+#pragma unroll
+            for (int r = 0; r < S::kRows; ++r) convert(op + r * kRowBytes, cb.a[r]);
             if (cb.nb == 2) {
-                convert(op + kOpSlotBytes, cb.b0);
-                if constexpr (kPairRows == 2) convert(op + kOpSlotBytes + kHalfRows, cb.b1);
+#pragma unroll
+                for (int r = 0; r < S::kRows; ++r) convert(op + kOpSlotBytes + r * kRowBytes, cb.b[r]);
             }
             dev::fence_proxy_async_smem();            // operand visible to the tensor core
             __syncwarp();
@@ -1059,9 +1074,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
             return true;
         };
+        static_assert(S::kBufs == 3 || S::kBufs == 4, "the rotations below use three or four buffers");
         Buf x, y, z, w;
-        x.own = y.own = z.own = w.own = kNoPacket;
-        if constexpr (kPackets) {
+#pragma unroll
+        for (int q = 0; q < kOwn; ++q) x.own[q] = y.own[q] = z.own[q] = w.own[q] = kNoPacket;
+        if constexpr (S::kBufs == 4) {
             next_owners(x);                           // stages 0, 1, 2, 3
             next_owners(y);
             next_owners(z);
@@ -1079,8 +1096,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 if (!step(z, w)) break;
             }
         } else {
+            next_owners(x);                           // stages 0, 1, 2
+            next_owners(y);
+            next_owners(z);
             issue(x);
+            next_owners(x);                           // stage 3
             issue(y);
+            next_owners(y);                           // stage 4
             for (;;) {
                 if (!step(z, x)) break;
                 if (!step(x, y)) break;
@@ -1280,7 +1302,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             const uint32_t pw = (uint32_t)std::min(64, s.n_inputs);
             const uint64_t dims[3] = {(uint64_t)s.n_inputs, (uint64_t)s.n_chan, (uint64_t)s.n_time};
             const uint64_t strides[2] = {(uint64_t)s.n_inputs, (uint64_t)s.n_inputs * s.n_chan};
-            const uint32_t box[3] = {pw, 1, (uint32_t)kKtMN};
+            const uint32_t box[3] = {pw, 1, (uint32_t)kt_of(engine, pk != nullptr)};
             enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(jobs[j].frame), dims,
                                strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
             d.pw = (int)pw;
@@ -1319,7 +1341,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             ms_max = std::max(ms_max, d.max_strip);
             d.strips = strips_per_channel(g.nb, d.max_strip);
         }
-        d.k_tiles = g.k_tiles;
+        d.k_tiles = (int)((s.n_time + kt_of(engine, pk != nullptr) - 1) / kt_of(engine, pk != nullptr));
         d.item_begin = items;
         const int64_t add = (int64_t)d.strips * s.n_chan;
         if (items + add > INT32_MAX / 2) return XE_EINVAL;
@@ -1328,7 +1350,8 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     if (nj == 0) return XE_OK;
     hp.n_jobs = nj;
     hp.n_items = items;
-    hp.k_flush_tiles = tune.k_flush / kt_of(engine);
+    // drain at least once per stage; a stage (<= 256 samples) never exceeds the exactness bound
+    hp.k_flush_tiles = std::max(1, tune.k_flush / kt_of(engine, pk != nullptr));
     hp.slots = ms_max == 1 ? 2 : (ms_max == 2 ? 3 : 4);     // operand blocks per stage for the widest strip
     hp.n_acc = ms_max <= 2 ? 2 : 1;                        // TMEM accumulators (each <= 256 columns)
     hp.status = status;
@@ -1336,7 +1359,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     hp.limit_ns = wait_limit_ns();
     const int bar_bytes = 1024;
     const int avail = kSmemMax - 1024 - bar_bytes;
-    const int op_slot = kBlk * kt_of(engine), pk_slot = 64 * kt_of(engine);
+    const int op_slot = kBlk * kt_of(engine, pk != nullptr), pk_slot = 64 * kt_of(engine);
     if (engine == kFusedPair) {
         hp.slots = kPairSlots;
         hp.n_acc = 2;
