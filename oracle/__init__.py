@@ -56,6 +56,9 @@ class Oracle:
         L.xo_assemble.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
                                   ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.xo_flag_counts.argtypes = [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.c_void_p]
         L.xo_counts_from_mask.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_void_p]
         L.xo_counts_from_counters.argtypes = [ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
@@ -121,6 +124,20 @@ class Oracle:
         if st != OK:
             raise ValueError("xo_assemble: invalid arguments")
         return frame, filled, lost, stats
+
+    def flag_counts(self, pkts: np.ndarray, seq0: int, gps: int, n_inputs: int, n_chan: int, n_time: int,
+                    flag_count: np.ndarray | None = None, flag_pairs: np.ndarray | None = None):
+        """F-engine flags from the packets' footers (Sec. II-C) -> (flag_count [F][N], flag_pairs [F][P]),
+        accumulated onto the given arrays."""
+        pkts = np.ascontiguousarray(pkts, dtype=np.uint8)
+        n = pkts.shape[0] if pkts.ndim == 2 else 0
+        stride = pkts.shape[1] if pkts.ndim == 2 and pkts.shape[0] else 16 + 36 * n_inputs
+        fc = np.zeros((n_chan, n_inputs), np.uint32) if flag_count is None else flag_count
+        fp = np.zeros((n_chan, self.npairs(n_inputs)), np.uint32) if flag_pairs is None else flag_pairs
+        st = self.L.xo_flag_counts(_ptr(pkts), n, stride, seq0, gps, n_inputs, n_chan, n_time, _ptr(fc), _ptr(fp))
+        if st != OK:
+            raise ValueError("xo_flag_counts: invalid arguments")
+        return fc, fp
 
     def counts_from_mask(self, valid: np.ndarray) -> np.ndarray:
         valid = np.ascontiguousarray(valid, dtype=np.uint8)
@@ -192,6 +209,10 @@ def correlate_pairs(frame, f, pairs):
 
 def assemble(pkts, seq0, gps, n_inputs, n_chan, n_time, lost=None, stats=None):
     return default().assemble(pkts, seq0, gps, n_inputs, n_chan, n_time, lost, stats)
+
+
+def flag_counts(pkts, seq0, gps, n_inputs, n_chan, n_time, flag_count=None, flag_pairs=None):
+    return default().flag_counts(pkts, seq0, gps, n_inputs, n_chan, n_time, flag_count, flag_pairs)
 
 
 def counts_from_mask(valid):

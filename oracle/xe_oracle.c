@@ -168,6 +168,53 @@ int xo_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
 }
 
 /*
+ * F-engine flags of one frame (Sec. II-C: flags for each input, frequency and time sample arrive in
+ * the packets' footers; flagged samples are already zero in the data). Footer reading used here:
+ * at byte 16 + 32N of a packet, [4 t][8 f][N/8] bytes, bit n % 8 of byte n / 8 set when input n is
+ * flagged. Packets are replayed in arrival order with the assembly's rules (first arrival of a
+ * slot wins; late, early, invalid and duplicate packets are ignored); a missing packet flags
+ * nothing (its samples are lost, not flagged).
+ * Outputs (accumulated): flag_count [F][N] += flagged samples of input n in channel f;
+ * flag_pairs [F][P] += samples in which inputs i and j (i <= j) are both flagged.
+ */
+int xo_flag_counts(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int gps,
+                   int N, int F, int T, uint32_t *flag_count, uint32_t *flag_pairs) {
+    if (N <= 0 || N % 8 || F <= 0 || T <= 0 || (T % 4) || (F % 8) || gps <= 0 || ((F / 8) % gps))
+        return XO_EINVAL;
+    const uint32_t footer = 16u + 32u * (uint32_t)N;
+    if (pkt_stride < footer + 4u * (uint32_t)N) return XO_EINVAL;
+    const int Q = T / 4, G = F / 8, S = G / gps;
+    const int64_t P = xo_npairs(N);
+    uint8_t *seen = calloc((size_t)Q * G, 1);
+    if (!seen) return XO_EINVAL;
+    for (uint32_t k = 0; k < n_pkts; ++k) {
+        const uint8_t *p = pkts + (size_t)k * pkt_stride;
+        uint16_t sid, grp;
+        uint64_t seq;
+        memcpy(&sid, p + 0, 2);
+        memcpy(&grp, p + 2, 2);
+        memcpy(&seq, p + 8, 8);
+        if (sid >= S || grp >= gps || seq < seq0 || seq - seq0 >= (uint64_t)Q) continue;
+        const int slot = (int)(seq - seq0), g = sid * gps + grp;
+        if (seen[(size_t)slot * G + g]) continue;
+        seen[(size_t)slot * G + g] = 1;
+        for (int tt = 0; tt < 4; ++tt)
+            for (int ff = 0; ff < 8; ++ff) {
+                const uint8_t *bits = p + footer + ((size_t)tt * 8 + ff) * (N / 8);
+                const int f = 8 * g + ff;
+                for (int i = 0; i < N; ++i) {
+                    if (!((bits[i / 8] >> (i % 8)) & 1)) continue;
+                    flag_count[(size_t)f * N + i] += 1;
+                    for (int j = i; j < N; ++j)
+                        if ((bits[j / 8] >> (j % 8)) & 1) flag_pairs[(size_t)f * P + xo_pidx(i, j, N)] += 1;
+                }
+            }
+    }
+    free(seen);
+    return XO_OK;
+}
+
+/*
  * Per-visibility sample counts by brute force: n_ij = sum_t [valid_i(t) and valid_j(t)].
  * valid: [T][F][N] bytes, nonzero = the sample entered the correlation (Sec. II-C: lost or
  * flagged samples are zeroed before correlation). n: uint32 [F][P].

@@ -148,12 +148,25 @@ def make_header(stream_id: int, chan_group: int, seq: int) -> np.ndarray:
     return h
 
 
-def packetize(frame: np.ndarray, seq0: int, groups_per_stream: int) -> np.ndarray:
+def footer_bytes(n_inputs: int) -> int:
+    """Flag footer of a packet: one bit per (sample, channel, input) = 4 x 8 x N bits."""
+    return 4 * CHANNELS_PER_GROUP * n_inputs // 8
+
+
+def packetize(frame: np.ndarray, seq0: int, groups_per_stream: int, flags: np.ndarray | None = None) -> np.ndarray:
     """Split a frame [T][F][N] into packets, in natural send order (seq, then stream, then group).
 
     Channel group G = stream_id * groups_per_stream + chan_group covers channels [8G, 8G+8).
-    Returns uint8 [n_packets][16 + 32N].
+    Returns uint8 [n_packets][16 + 32N]. With `flags` (bool [T][F][N], the F-engine's flags) the
+    flagged samples are zeroed in the payload and each packet carries a footer of 4N bytes after
+    it: [4 t][8 f][N/8], bit n % 8 of byte n / 8 set for a flagged input n; records are then
+    16 + 36N bytes.
     """
+    if flags is not None:
+        flags = np.asarray(flags, dtype=bool)
+        if flags.shape != frame.shape:
+            raise ValueError("flags must have the frame's shape")
+        frame = np.where(flags, np.uint8(0), frame)
     T, F, N = frame.shape
     G = F // CHANNELS_PER_GROUP
     if T % SAMPLES_PER_PACKET or F % CHANNELS_PER_GROUP or G % groups_per_stream:
@@ -169,7 +182,12 @@ def packetize(frame: np.ndarray, seq0: int, groups_per_stream: int) -> np.ndarra
     hdr[..., 0:2] = np.broadcast_to(sid, (Q, n_streams, groups_per_stream)).astype("<u2")[..., None].view(np.uint8)
     hdr[..., 2:4] = np.broadcast_to(grp, (Q, n_streams, groups_per_stream)).astype("<u2")[..., None].view(np.uint8)
     hdr[..., 8:16] = np.broadcast_to(seq, (Q, n_streams, groups_per_stream)).astype("<u8")[..., None].view(np.uint8)
-    return np.concatenate([hdr.reshape(Q * G, HEADER_BYTES), pay], axis=1)
+    parts = [hdr.reshape(Q * G, HEADER_BYTES), pay]
+    if flags is not None:
+        fl = flags.reshape(Q, SAMPLES_PER_PACKET, n_streams, groups_per_stream, CHANNELS_PER_GROUP, N)
+        fl = fl.transpose(0, 2, 3, 1, 4, 5).reshape(Q * G, SAMPLES_PER_PACKET * CHANNELS_PER_GROUP, N)
+        parts.append(np.packbits(fl, axis=2, bitorder="little").reshape(Q * G, footer_bytes(N)))
+    return np.concatenate(parts, axis=1)
 
 
 def network_order(n_packets: int, seed: int, p_drop: float = 0.0, p_reorder: float = 0.0,
@@ -195,9 +213,9 @@ def network_order(n_packets: int, seed: int, p_drop: float = 0.0, p_reorder: flo
 
 def packet_stream(frame: np.ndarray, seq0: int, groups_per_stream: int, seed: int,
                   p_drop: float = 0.0, p_reorder: float = 0.0, p_dup: float = 0.0,
-                  max_disp: int = 64) -> np.ndarray:
+                  max_disp: int = 64, flags: np.ndarray | None = None) -> np.ndarray:
     """Packets of ``frame`` as they arrive: natural send order perturbed by :func:`network_order`."""
-    pk = packetize(frame, seq0, groups_per_stream)
+    pk = packetize(frame, seq0, groups_per_stream, flags)
     order = network_order(pk.shape[0], seed, p_drop, p_reorder, p_dup, max_disp)
     return np.ascontiguousarray(pk[order])
 
@@ -225,6 +243,22 @@ def packetize_torch(frame, seq0: int, groups_per_stream: int):
     hdr[..., 2] = seq          # low 32 bits of the little-endian u64; high word stays 0
     out[:, :HEADER_BYTES] = hdr.reshape(Q * G, 4).view(torch.uint8).reshape(Q * G, HEADER_BYTES)
     return out
+
+
+def random_flags(n_time: int, n_chan: int, n_inputs: int, seed: int, p_sample: float = 0.002,
+                 p_burst: float = 0.02, p_all: float = 0.002) -> np.ndarray:
+    """F-engine flags, bool [T][F][N] (seeded): isolated flagged samples (p_sample per sample),
+    bursts on one input (an input of a channel flagged for 16 consecutive samples, p_burst per input
+    and channel), and samples in which every input of a channel is flagged (p_all per sample and
+    channel: the dense case of the pair intersections)."""
+    rng = np.random.default_rng(seed)
+    fl = rng.random((n_time, n_chan, n_inputs)) < p_sample
+    bursts = np.argwhere(rng.random((n_chan, n_inputs)) < p_burst)
+    for f, n in bursts:
+        t0 = int(rng.integers(0, max(1, n_time - 16)))
+        fl[t0:t0 + 16, f, n] = True
+    fl |= (rng.random((n_time, n_chan)) < p_all)[:, :, None]
+    return fl
 
 
 def config4_shapes(seed: int = 4, n_jobs: int = 24):

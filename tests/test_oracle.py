@@ -329,10 +329,70 @@ def pin_table1_geometry(o):
     assert round(out_sys / 1e6, 1) == g["output_per_10s"]["system"]
 
 
+def _brute_flag_counts(flags):
+    T, F, N = flags.shape
+    c = flags.sum(0).astype(np.uint32)
+    iu = np.triu_indices(N)
+    x = np.stack([(flags[:, f, :, None] & flags[:, f, None, :]).sum(0)[iu] for f in range(F)]).astype(np.uint32)
+    return c, x
+
+
+def pin_flag_footer_layout(o):
+    """Footer reading (Sec. II-C flags as packet bit fields): one flagged sample (t=6, f=11, n=13)
+    sets exactly bit 13 % 8 of byte 13 / 8 of row (t % 4) * 8 + f % 8 of the footer of slot t / 4,
+    group f / 8, and counts once for input 13 and once for the pair (13, 13). With the footer a
+    packet is 16 + 36N bytes: 9,232 B at N = 256, the paper's ~9 kB packet."""
+    N, F, T = 16, 16, 16
+    fl = np.zeros((T, F, N), bool)
+    fl[6, 11, 13] = True
+    pk = synth.packetize(synth.uniform_frame(N, F, T, 3), 0, 1, fl)
+    assert pk.shape[1] == 16 + 36 * N and 16 + 36 * 256 == 9232
+    k = 1 * 2 + 1                                                    # slot 1, group 1 (2 groups)
+    foot = pk[:, 16 + 32 * N:]
+    row = (6 % 4) * 8 + 11 % 8
+    assert foot[k, row * (N // 8) + 13 // 8] == 1 << (13 % 8) and foot.sum() == foot[k].sum() == 1 << (13 % 8)
+    assert pk[k, 16 + row * N + 13] == 0                              # the flagged sample is zero in the data
+    c, x = o.flag_counts(pk, 0, 1, N, F, T)
+    assert c.sum() == 1 and c[11, 13] == 1
+    assert x.sum() == 1 and x[11, o.pidx(13, 13, N)] == 1
+
+
+def pin_flag_counts_brute_force(o):
+    """Flag counts of a frame delivered with loss, reordering and duplicates equal the per-input
+    sums and pair intersections of the flags of the samples that arrived (lost slots flag
+    nothing), counted directly from the flag array."""
+    N, F, T, gps = 24, 16, 64, 2
+    fr = synth.signal_frame(N, F, T, 33)
+    fl = synth.random_flags(T, F, N, 34, p_sample=0.03, p_burst=0.1, p_all=0.02)
+    pk = synth.packet_stream(fr, 0, gps, 35, p_drop=0.1, p_reorder=0.2, p_dup=0.1, flags=fl)
+    _, filled, _, _ = o.assemble(pk, 0, gps, N, F, T)
+    present = np.repeat(np.repeat(filled.astype(bool), 4, axis=0), 8, axis=1)     # [T][F]
+    c, x = o.flag_counts(pk, 0, gps, N, F, T)
+    bc, bx = _brute_flag_counts(fl & present[:, :, None])
+    np.testing.assert_array_equal(c, bc)
+    np.testing.assert_array_equal(x, bx)
+    assert c.sum() > 0 and (x.sum() > c.sum())                       # some pairs flagged together
+
+
+def pin_flag_counts_give_mask_counts(o):
+    """Sec. II-C end to end: loss counters from the assembly and flag counters from the footers,
+    combined by the counter scheme, give the brute-force count of samples valid for both inputs."""
+    N, F, T, gps = 16, 8, 128, 1
+    fr = synth.signal_frame(N, F, T, 36)
+    fl = synth.random_flags(T, F, N, 37, p_sample=0.02, p_burst=0.05, p_all=0.01)
+    pk = synth.packet_stream(fr, 0, gps, 38, p_drop=0.05, p_reorder=0.1, flags=fl)
+    _, filled, lost, _ = o.assemble(pk, 0, gps, N, F, T)
+    c, x = o.flag_counts(pk, 0, gps, N, F, T)
+    present = np.repeat(np.repeat(filled.astype(bool), 4, axis=0), 8, axis=1)
+    valid = present[:, :, None] & ~fl
+    np.testing.assert_array_equal(o.counts_from_counters(T, lost, N, c, x), o.counts_from_mask(valid.astype(np.uint8)))
+
+
 PINS = [pin_sample_decode, pin_pidx_bijection, pin_brute_force, pin_pairs, pin_library_gram, pin_subset_channels,
         pin_autocorrelation, pin_constant_input, pin_single_source, pin_overflow_bound,
         pin_assembly_basic, pin_assembly_permutation, pin_assembly_loss_and_dups, pin_assembly_window,
-        pin_counts_counters_equal_mask, pin_normalize, pin_table1_geometry]
+        pin_counts_counters_equal_mask, pin_normalize, pin_table1_geometry, pin_flag_footer_layout,
+        pin_flag_counts_brute_force, pin_flag_counts_give_mask_counts]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])

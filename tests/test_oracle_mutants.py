@@ -48,6 +48,13 @@ MUTANTS = {
     "late_early_swapped": ("if (seq < seq0) { stats[2]++; continue; }", "if (seq < seq0) { stats[3]++; continue; }"),
     # intersection correction with the wrong sign
     "intersection_sign": ("- flag_pairs[(size_t)f * P + p];", "+ flag_pairs[(size_t)f * P + p];"),
+    # flag pair intersections without the diagonal (i == j)
+    "flag_pairs_no_diagonal": ("for (int j = i; j < N; ++j)\n                        if ((bits[j / 8] >> (j % 8)) & 1)",
+                               "for (int j = i + 1; j < N; ++j)\n                        if ((bits[j / 8] >> (j % 8)) & 1)"),
+    # flags of duplicate packets counted again
+    "flags_of_duplicates": ("if (seen[(size_t)slot * G + g]) continue;", "(void)0;"),
+    # footer bits read most significant first
+    "flag_bit_order": ("if (!((bits[i / 8] >> (i % 8)) & 1)) continue;", "if (!((bits[i / 8] >> (7 - i % 8)) & 1)) continue;"),
     # normalisation applied as a product instead of a quotient
     "normalize_product": ("out[2 * q] = (float)((double)vis[2 * q] / (double)n[q]);",
                           "out[2 * q] = (float)((double)vis[2 * q] * (double)n[q]);"),
