@@ -212,6 +212,27 @@ int xe_correlate_packets(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stri
                          uint8_t *filled, uint32_t *lost, uint32_t *stats, void *ws, size_t ws_bytes,
                          void *stream);
 
+/*
+ * F-engine flags of one frame (Sec. II-C: the F-engine flags samples of individual inputs,
+ * frequencies and times, sends the flags as bit fields with the data and zeroes the flagged samples;
+ * the X-engine counts them per input and, per sample, the inputs flagged together). Footer reading
+ * used: at byte 16 + 32N of each packet record, [4 t][8 f][N/8] bytes, bit n % 8 of byte n / 8 set
+ * when input n is flagged (records of at least 16 + 36N bytes; 9,232 B at N = 256). Packets are
+ * placed as xe_assemble places them (first arrival of a slot wins; late, early, invalid and
+ * duplicate packets are ignored); a missing packet flags nothing (its samples are lost instead).
+ *
+ *   pkts, n_pkts, pkt_stride, seq0, groups_per_stream, s: as xe_assemble.
+ *   flag_count  in/out, uint32 [F][N]; += flagged samples of input n in channel f.
+ *   flag_pairs  in/out, uint32 [F][P]; += samples in which inputs i <= j are both flagged.
+ *   ws          workspace of xe_flag_counts_workspace_size(s) bytes (any contents).
+ * Feed both to xe_normalize. Cost grows with E^2 for E inputs flagged in one sample.
+ * Errors: XE_EINVAL (geometry, records without a footer, alignment), XE_ENOMEM, XE_ECUDA.
+ */
+size_t xe_flag_counts_workspace_size(xe_shape s);
+int xe_flag_counts(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
+                   int32_t groups_per_stream, xe_shape s, uint32_t *flag_count, uint32_t *flag_pairs,
+                   void *ws, size_t ws_bytes, void *stream);
+
 /* ---------------------------------------------------------------- A5: normalisation (Sec. II-C) */
 
 /*

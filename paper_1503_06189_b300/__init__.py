@@ -25,7 +25,8 @@ EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",
     "xe_assemble_workspace_size", "xe_assemble", "xe_assemble_noalloc", "xe_unpack", "xe_correlate_workspace_size",
     "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched",
-    "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_normalize",
+    "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_flag_counts_workspace_size",
+    "xe_flag_counts", "xe_normalize",
     "xe_stream_create", "xe_stream_submit", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
     "xe_stream_stats", "xe_stream_destroy",
 ]
@@ -109,6 +110,9 @@ def _load():
     L.xe_correlate_packets_workspace_size.restype = sz
     L.xe_correlate_packets_workspace_size.argtypes = [Shape]
     L.xe_correlate_packets.argtypes = [vp, u32, u32, u64, i32, Shape, vp, ctypes.c_int, vp, vp, vp, vp, sz, vp]
+    L.xe_flag_counts_workspace_size.restype = sz
+    L.xe_flag_counts_workspace_size.argtypes = [Shape]
+    L.xe_flag_counts.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, vp, sz, vp]
     L.xe_normalize.argtypes = [vp, Shape, u32, vp, vp, vp, vp, vp, vp]
     L.xe_stream_create.argtypes = [ctypes.POINTER(StreamCfg), ctypes.POINTER(vp)]
     L.xe_stream_submit.argtypes = [vp, i32, vp, u32]
@@ -266,6 +270,17 @@ def xe_correlate_batched(jobs, ws, tune=None, stream=None):
     arr = _jobs(jobs)
     _check(_L.xe_correlate_batched(arr, len(jobs), _tune(tune), _ptr(ws), _nbytes(ws), _stream(stream)),
            "xe_correlate_batched")
+
+
+def xe_flag_counts_workspace_size(shape: Shape) -> int:
+    return _L.xe_flag_counts_workspace_size(shape)
+
+
+def xe_flag_counts(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
+                   flag_count, flag_pairs, ws, stream=None):
+    """F-engine flags from the packets' footers: += per-input counts and pair intersections."""
+    _check(_L.xe_flag_counts(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(flag_count),
+                             _ptr(flag_pairs), _ptr(ws), _nbytes(ws), _stream(stream)), "xe_flag_counts")
 
 
 def xe_correlate_packets_workspace_size(shape: Shape) -> int:

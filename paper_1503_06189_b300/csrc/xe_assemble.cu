@@ -99,6 +99,56 @@ __global__ void tally_kernel(const uint8_t *__restrict__ pkts, Geo g, const uint
     }
 }
 
+// F-engine flags (Sec. II-C): one warp per packet; a packet that owns its slot adds the flags of its
+// footer (at byte `footer`: [4 t][8 f][N/8] bytes, bit n % 8 of byte n / 8 = input n flagged) to the
+// per-input counts count[f][n] and the pair intersections pairs[f][p(i,j)], i <= j. A row with E
+// flagged inputs costs E (E + 1) / 2 atomic adds, spread over the warp; rows without flags are
+// skipped after one warp vote.
+constexpr int kFlagThreads = 128;
+
+__global__ void __launch_bounds__(kFlagThreads) flags_kernel(const uint8_t *__restrict__ pkts, Geo g,
+                                                            const uint32_t *__restrict__ owner, uint32_t footer,
+                                                            uint32_t *count, uint32_t *pairs) {
+    __shared__ uint16_t list[kFlagThreads / 32][4096];
+    __shared__ int n_set[kFlagThreads / 32];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t k = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    if (k >= g.n_pkts) return;
+    int slot = 0, grp = 0;
+    if (classify(pkts, g, (uint32_t)k, slot, grp) != kOk) return;
+    if (owner[oidx(g, slot, grp)] != (uint32_t)k) return;          // duplicate: its first arrival counts
+    const int N = g.N, NB = N / 8;
+    const int64_t P = npairs(N);
+    const uint8_t *foot = pkts + (size_t)k * g.stride + footer;
+    for (int row = 0; row < 32; ++row) {                             // (t % 4, f % 8) = (row / 8, row % 8)
+        const uint8_t *bits = foot + (size_t)row * NB;
+        int any = 0;
+        for (int b = lane; b < NB; b += 32) any |= bits[b];
+        if (!__any_sync(0xffffffffu, any)) continue;
+        const int f = 8 * grp + (row & 7);
+        if (lane == 0) n_set[w] = 0;
+        __syncwarp();
+        for (int b = lane; b < NB; b += 32) {
+            for (uint32_t v = bits[b]; v; v &= v - 1) {
+                const int i = 8 * b + __ffs(v) - 1;
+                list[w][atomicAdd(&n_set[w], 1)] = (uint16_t)i;
+                atomicAdd(&count[(size_t)f * N + i], 1u);
+            }
+        }
+        __syncwarp();
+        const int E = n_set[w];
+        for (int a = 0; a < E; ++a) {
+            const int ia = list[w][a];
+            for (int b = a + lane; b < E; b += 32) {
+                const int ib = list[w][b];
+                const int i = min(ia, ib), j = max(ia, ib);
+                atomicAdd(&pairs[(size_t)f * P + (int64_t)i * N - (int64_t)i * (i - 1) / 2 + (j - i)], 1u);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // One warp per packet (warps [0, n_pkts)) and one warp per (slot, group) (the warps after them).
 // Blocks of 128 threads: small enough to run beside the correlation kernel on the same SM, so the
 // assembly of one frame can overlap the correlation of the previous one.
@@ -155,6 +205,51 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
                 size_t ws_bytes, void *stream) {
     return xe::assemble_streams(pkts, n_pkts, pkt_stride, seq0, gps, 0, s, frame, filled, lost, stats, ws, ws_bytes,
                                 static_cast<cudaStream_t>(stream));
+}
+
+size_t xe_flag_counts_workspace_size(xe_shape s) {
+    if (!valid_shape(s) || s.n_time % 4 || s.n_chan % 8) return 0;
+    return (size_t)round_up((int64_t)(s.n_time / 4) * (s.n_chan / 8), 64) * 4 + 256;
+}
+
+int xe_flag_counts(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0, int32_t gps, xe_shape s,
+                   uint32_t *flag_count, uint32_t *flag_pairs, void *ws, size_t ws_bytes, void *stream) {
+    if (!valid_shape(s) || s.n_time < 4 || s.n_time % 4 || s.n_chan % 8 || gps < 1 || (s.n_chan / 8) % gps)
+        return XE_EINVAL;
+    if (!flag_count || !flag_pairs || (n_pkts && !pkts)) return XE_EINVAL;
+    const uint32_t footer = 16u + 32u * (uint32_t)s.n_inputs;
+    if (pkt_stride % 16 || pkt_stride < footer + 4u * (uint32_t)s.n_inputs) return XE_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(pkts) & 15) || (reinterpret_cast<uintptr_t>(ws) & 3) ||
+        (reinterpret_cast<uintptr_t>(flag_count) & 3) || (reinterpret_cast<uintptr_t>(flag_pairs) & 3))
+        return XE_EINVAL;
+    if (!ws || ws_bytes < xe_flag_counts_workspace_size(s)) return XE_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    asmb::Geo g;
+    g.seq0 = seq0;
+    g.n_pkts = n_pkts;
+    g.stride = pkt_stride;
+    g.N = s.n_inputs;
+    g.F = s.n_chan;
+    g.Q = s.n_time / 4;
+    g.G = s.n_chan / 8;
+    g.gps = gps;
+    g.S = g.G / gps;
+    uint32_t *owner = static_cast<uint32_t *>(ws);
+    const int64_t slots = (int64_t)g.Q * g.G;
+    uint32_t *scratch = owner + round_up(slots, 64);             // the claim's late / early counters
+    XE_TRY_CUDA(cudaMemsetAsync(scratch, 0, 32, st));
+    asmb::init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
+    XE_TRY_CUDA(cudaGetLastError());
+    if (n_pkts) {
+        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, scratch);
+        XE_TRY_CUDA(cudaGetLastError());
+        const uint64_t blocks = ((uint64_t)n_pkts * 32 + asmb::kFlagThreads - 1) / asmb::kFlagThreads;
+        if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
+        asmb::flags_kernel<<<(unsigned)blocks, asmb::kFlagThreads, 0, st>>>(pkts, g, owner, footer, flag_count,
+                                                                             flag_pairs);
+        XE_TRY_CUDA(cudaGetLastError());
+    }
+    return XE_OK;
 }
 
 }  // extern "C"
