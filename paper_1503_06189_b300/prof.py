@@ -4,6 +4,7 @@
     python -m paper_1503_06189_b300.prof assemble  --n 256 --f 128 --t 4096 --iters 3
     python -m paper_1503_06189_b300.prof normalize --n 256 --f 128 --iters 3
     python -m paper_1503_06189_b300.prof packets   --n 256 --f 128 --t 4096 --iters 3
+    python -m paper_1503_06189_b300.prof flags     --n 256 --f 256 --t 4096 --iters 3
 
 Inputs are uniform random bytes generated on the device; sizes default to a frame larger than L2
 (128 MiB) so that DRAM counters are meaningful, while the device footprint stays at a few GB.
@@ -21,7 +22,7 @@ import paper_1503_06189_b300 as xe
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["correlate", "assemble", "normalize", "packets"])
+    ap.add_argument("op", choices=["correlate", "assemble", "normalize", "packets", "flags"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--f", type=int, default=128)
     ap.add_argument("--t", type=int, default=4096)
@@ -112,6 +113,28 @@ def main(argv=None):
             best = min(ms[1:] if len(ms) > 1 else ms)
             print(f"packets {name} N={N} F={F} T={T}: best {best:.4f} ms, {cmac / best / 1e9:.3f} TCMAC/s",
                   flush=True)
+    elif a.op == "flags":
+        # flag counts from packet footers: sparse flags, bursts and a few fully flagged samples
+        import numpy as np
+
+        import synth
+        host = frame.cpu().numpy()
+        del frame
+        fl = synth.random_flags(T, F, N, 5, p_sample=0.001, p_burst=0.01, p_all=0.001)
+        pk = torch.from_numpy(synth.packetize(host, 0, 1, fl)).to(dev)
+        fc = torch.zeros((F, N), dtype=torch.int32, device=dev)
+        fp = torch.zeros((F, P), dtype=torch.int32, device=dev)
+        ws = torch.empty(xe.xe_flag_counts_workspace_size(s), dtype=torch.uint8, device=dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.iters)]
+        for e0, e1 in evs:
+            e0.record()
+            xe.xe_flag_counts(pk, pk.shape[0], pk.shape[1], 0, 1, s, fc, fp, ws)
+            e1.record()
+        torch.cuda.synchronize()
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        best = min(ms[1:] if len(ms) > 1 else ms)
+        print(f"flags N={N} F={F} T={T}: best {best:.4f} ms for {pk.numel() / 1e6:.0f} MB of packets, "
+              f"{float(np.mean(fl)) * 100:.3f}% of samples flagged", flush=True)
     else:
         lost = torch.zeros(F, dtype=torch.int32, device=dev)
         out = torch.empty((F, P, 2), dtype=torch.float32, device=dev)
