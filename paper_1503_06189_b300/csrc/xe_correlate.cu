@@ -656,11 +656,11 @@ struct PairShape {
 constexpr int kPairMaxStages = 6;
 constexpr int kPairPrefetch = 4;              // L2 prefetch distance in stages
 
-// Work items of one job with doubles (packet mode), in this order: first the "doubles" of all
-// channels, then the single blocks of all channels (so that every pair gets a share of both kinds):
-// 2 items per channel instead of 3 at N = 256, 25 % fewer conversions and sample gathers, 1.02 ->
-// 0.88 ms per full-band frame. (Frame mode, with 256-sample stages, runs every block as its own item:
-// doubles make its stages MMA-bound, 0.80 -> 0.84 ms.) A double is the diagonal block
+// Work items of one job with doubles (packet mode), channel by channel: the channel's doubles, then
+// its single blocks: 2 items per channel instead of 3 at N = 256, 25 % fewer conversions and sample
+// gathers. Pairs take items pair, pair + pairs, ...; the launch uses an odd number of pairs, so a
+// pair alternates between doubles and singles. (Frame mode, with 256-sample stages, runs every block
+// as its own item: doubles make its stages MMA-bound, 0.80 -> 0.84 ms.) A double is the diagonal block
 // (R, R) together with its right neighbour (R, R + 1), R < S2 - 1: both multiply the same A block, so
 // they are computed together into the two TMEM halves from one converted operand stage (A, B =
 // block R + 1). Singles are the blocks (R, C), C >= R + 2, and the last diagonal block (S2 - 1,
@@ -684,17 +684,15 @@ __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &jo
         C = R + q;
         return;
     }
-    if (l < jb.n_chan * D) {
-        f = l / D;
-        R = l % D;
+    f = l / jb.strips;
+    int q = l % jb.strips;
+    if (q < D) {
+        R = q;
         C = R + 1;
         dbl = true;
         return;
     }
-    l -= jb.n_chan * D;
-    const int singles = jb.strips - D;
-    f = l / singles;
-    int q = l % singles;
+    q -= D;
     dbl = false;
     for (R = 0; R < S2 - 1; ++R) {
         if (q < S2 - R - 2) break;
@@ -1034,22 +1032,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 const bool add = jb.accumulate || k0 > 0;
                 const uint32_t tb = tmem + acc * 256u + (uint32_t(q * 32) << 16);
                 auto jb_of = [&](int ck) { return (cb0 * kBlk + ck * 32) / 2 + (im_row ? 8 : 0); };
-                int2 old[8];
+                int2 old[8], nxt[8];
                 int ck = half;
                 if (add && ck < n_chunks) load_old(vis_f, prow, i, jb_of(ck), N, i_ok, old);
                 else {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) old[k] = make_int2(0, 0);
                 }
-                // (the old values of the next chunk are read after this chunk's store: the epilogue has
-                // slack, and a look-ahead buffer would cost the converter warps registers)
+                // frame mode reads the next chunk's old values after this chunk's store (a look-ahead
+                // buffer would cost its 80-register converter warps); packet mode, whose epilogue drains
+                // both halves of a double item, reads them ahead
 #pragma unroll 1
                 for (; ck < n_chunks; ck += kPerQuarter) {
                     const bool more = ck + kPerQuarter < n_chunks;
+                    if constexpr (kPackets) {
+                        if (add && more) load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, nxt);
+                    }
                     int vr[8], vi[8];
                     combine_chunk<true>(tb + ck * 32, im_row, vr, vi);
                     store_vis(vis_f, prow, i, jb_of(ck), N, i_ok, vr, vi, old);
-                    if (add && more) load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, old);
+                    if (add && more) {
+                        if constexpr (kPackets) {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) old[k] = nxt[k];
+                        } else {
+                            load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, old);
+                        }
+                    }
                 }
                 dev::tc_fence_before();
                 __syncwarp();
@@ -1310,6 +1319,9 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaSt
     }
     int pairs = std::min(items, max_pairs[dev]);
     if (n_ctas > 0) pairs = std::max(1, std::min(pairs, n_ctas / 2));
+    // packet mode interleaves doubles and singles channel by channel: an odd pair count makes every
+    // pair alternate between the two kinds
+    if (kPackets && pairs > 1 && pairs % 2 == 0) --pairs;
     correlate_pair_kernel<kPackets><<<2 * pairs, PairShape<kPackets>::kThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;

@@ -29,6 +29,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--engine", type=int, default=0)
     ap.add_argument("--max-strip", type=int, default=0)
+    ap.add_argument("--accumulate", action="store_true", help="packets: add into the visibilities, as an integration does")
     ap.add_argument("--order", choices=["arrival", "group"], default="arrival",
                     help="packets: keep arrival (sequence-major) order or sort them group-major")
     ap.add_argument("--align", action="store_true",
@@ -95,11 +96,11 @@ def main(argv=None):
         wsc = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
 
         def zero_copy():
-            xe.xe_correlate_packets(pk, pk.shape[0], pk.shape[1], 0, 1, s, vis, False, filled, lost, stats, ws)
+            xe.xe_correlate_packets(pk, pk.shape[0], pk.shape[1], 0, 1, s, vis, a.accumulate, filled, lost, stats, ws)
 
         def two_step():
             xe.xe_assemble(pk, pk.shape[0], pk.shape[1], 0, 1, s, out, filled, lost, stats, wsa)
-            xe.xe_correlate(out, s, vis, False, wsc)
+            xe.xe_correlate(out, s, vis, a.accumulate, wsc)
 
         cmac = F * P * T
         for name, fn in (("zero-copy", zero_copy), ("two-step", two_step)):
