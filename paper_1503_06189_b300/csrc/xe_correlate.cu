@@ -1023,6 +1023,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             const int64_t prow = (int64_t)i * N - (int64_t)i * (i - 1) / 2 - i;
             int32_t *vis_f = jb.vis + (size_t)f * (size_t)npairs(N) * 2;
             const int n_chunks = 2 * (kBlk / 32);
+            if (kPackets && jb.accumulate && i_ok) {
+                // packet mode: the old values this item adds to go into L2 while its MMAs run (the
+                // drain of a half holds up the tensor core, a double item filling all of TMEM);
+                // frame mode measured slower with the prefetch
+                for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {
+                    const int jc = (2 * (dbl ? R + sub : C_item) * kBlk) / 2 + (im_row ? 8 : 0);
+#pragma unroll 1
+                    for (int ck = 0; ck < n_chunks; ++ck) {
+                        const int j0 = max(jc + 16 * ck, i), j1 = min(jc + 16 * ck + 7, N - 1);
+                        if (j0 > j1) continue;
+                        dev::prefetch_l2(vis_f + 2 * (prow + j0));
+                        dev::prefetch_l2(vis_f + 2 * (prow + j1));
+                    }
+                }
+            }
             for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles)
             for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {        // a double: block (R, R), then (R, R + 1)
                 const int C = dbl ? R + sub : C_item;

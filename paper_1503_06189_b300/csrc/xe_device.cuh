@@ -145,6 +145,11 @@ __device__ __forceinline__ uint4 ld_stream_16(const uint8_t *ptr) {
     return v;
 }
 
+// Hint: bring the 128-byte line holding ptr into L2 (no register result, no fault on the address).
+__device__ __forceinline__ void prefetch_l2(const void *ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 // ------------------------------------------------------------------ tcgen05 (TMEM + MMA)
 
 // Allocates `ncols` TMEM columns (power of two >= 32); the base address is written to smem.

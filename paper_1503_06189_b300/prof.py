@@ -29,7 +29,7 @@ def main(argv=None):
     ap.add_argument("--iters", type=int, default=3)
     ap.add_argument("--engine", type=int, default=0)
     ap.add_argument("--max-strip", type=int, default=0)
-    ap.add_argument("--accumulate", action="store_true", help="packets: add into the visibilities, as an integration does")
+    ap.add_argument("--accumulate", action="store_true", help="correlate, packets: add into the visibilities, as an integration does")
     ap.add_argument("--order", choices=["arrival", "group"], default="arrival",
                     help="packets: keep arrival (sequence-major) order or sort them group-major")
     ap.add_argument("--align", action="store_true",
@@ -46,7 +46,7 @@ def main(argv=None):
     t0 = time.perf_counter()
     if a.op == "correlate":
         tune = dict(engine=a.engine, max_strip=a.max_strip, k_flush=0, n_ctas=0)
-        jobs = [(frame, vis, s, False)]
+        jobs = [(frame, vis, s, a.accumulate)]
         ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device=dev)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.iters)]
         for e0, e1 in evs:
