@@ -238,10 +238,13 @@ def run_serving(xe, torch, dev, frames_per_stream: int = 8, seed: int = 5000, ri
 
 
 def workload_config(args):
+    G = args.frames_per_call
     return {"workload": f"full band batched: N={N_INPUTS}, F={N_CHAN} channels, {args.frames} frames x "
                         f"T={N_TIME} from 16-byte-header UDP packets (128 streams x 8 ch, 0.1% lost), "
-                        f"zero-copy assemble + correlate (accumulate) per frame, normalise per integration",
+                        f"zero-copy assemble + correlate (accumulate), {G} consecutive frame(s) per call "
+                        f"(T = {G * N_TIME} samples), normalise per integration",
             "n_inputs": N_INPUTS, "n_chan": N_CHAN, "n_time": N_TIME, "frames": args.frames,
+            "frames_per_call": G,
             "l2": "inputs larger than L2 (distinct packets per frame)",
             "parallelism": (f"channel shards x{args.gpus}: rank r correlates channels [1024 r, 1024 r + 1024) of a "
                             f"{1024 * args.gpus}-channel band from its own packets; no collective on the data path")}
@@ -249,13 +252,17 @@ def workload_config(args):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def make_packets(frames: int, device, seed: int = 3000, p_drop: float = 0.001):
-    """64 distinct frames of synthetic packets, generated on the device (torch RNG), 0.1% dropped."""
+def make_packets(frames: int, device, seed: int = 3000, p_drop: float = 0.001, frames_per_group: int = 1):
+    """64 distinct frames of synthetic packets, generated on the device (torch RNG), 0.1% dropped.
+    Returns per-frame views [n_k][stride] and their counts; the frames of each group of
+    frames_per_group consecutive frames lie back to back in one buffer, so that a group is also one
+    contiguous packet array (one call over T = frames_per_group x 4096 samples)."""
     import torch
 
     import synth
 
     pkts, counts = [], []
+    group = []
     for k in range(frames):
         fr = synth.signal_frame_torch(N_INPUTS, N_CHAN, N_TIME, seed + k, device=device, chunk=128)
         pk = synth.packetize_torch(fr, k * N_TIME // 4, GROUPS_PER_STREAM)
@@ -264,8 +271,15 @@ def make_packets(frames: int, device, seed: int = 3000, p_drop: float = 0.001):
         g.manual_seed(seed + 7 * k)
         keep = torch.rand(pk.shape[0], generator=g, device=device) >= p_drop
         pk = pk[keep].contiguous()
-        pkts.append(pk)
+        group.append(pk)
         counts.append(pk.shape[0])
+        if len(group) == frames_per_group or k == frames - 1:
+            buf = torch.cat(group) if len(group) > 1 else group[0]
+            group.clear()
+            off = 0
+            for c in counts[len(pkts):]:
+                pkts.append(buf[off:off + c])
+                off += c
     return pkts, counts
 
 
@@ -284,33 +298,52 @@ def run_xe(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    N, F, T, FR = N_INPUTS, N_CHAN, N_TIME, args.frames
-    s = xe.Shape(N, F, T)
-    pkts, counts = make_packets(FR, dev, seed=3000 + 100000 * rank)
+    N, F, T, FR, G = N_INPUTS, N_CHAN, N_TIME, args.frames, args.frames_per_call
+    if G < 1 or FR % G or G * T > 1 << 15:
+        raise SystemExit("--frames-per-call must divide --frames, with frames_per_call x 4096 <= 32768")
+    pkts, counts = make_packets(FR, dev, seed=3000 + 100000 * rank, frames_per_group=G)
     stride = pkts[0].shape[1]
-    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
+    filled = torch.empty((G * T // 4, F // 8), dtype=torch.uint8, device=dev)
     lost = torch.zeros(F, dtype=torch.int32, device=dev)
     stats = torch.zeros(5, dtype=torch.int32, device=dev)
     vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
     out = torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev)
-    ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device=dev)
+    ws = torch.empty(xe.xe_correlate_packets_workspace_size(xe.Shape(N, F, G * T)), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
     n_ev = FR * max(args.steps, 1)
     ev_c0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
     ev_c1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
-    launches_per_step = FR * 4 + 1                # per frame: init, claim, tally, correlation; + normalise
 
-    def step(ev_base=None):
-        with torch.cuda.stream(stream):
-            lost.zero_()
-        for k in range(FR):
-            if ev_base is not None:
-                ev_c0[ev_base + k].record(stream)
-            xe.xe_correlate_packets(pkts[k], counts[k], stride, k * T // 4, GROUPS_PER_STREAM, s, vis, k > 0,
-                                    filled, lost, stats, ws, stream=stream)
-            if ev_base is not None:
-                ev_c1[ev_base + k].record(stream)
-        xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=stream)
+    def calls(g):
+        """(packet view, count, seq0) of each call when g consecutive frames go into one call: the
+        frames of a call are contiguous in memory (groups of G, g dividing G)."""
+        out_ = []
+        for c in range(FR // g):
+            k0 = c * g
+            first = pkts[k0]
+            n = sum(counts[k0:k0 + g])
+            out_.append((first.as_strided((n, stride), (stride, 1)), n, k0 * T // 4))
+        return out_
+
+    def make_step(g):
+        cl = calls(g)
+        sg = xe.Shape(N, F, g * T)
+
+        def step(ev_base=None):
+            with torch.cuda.stream(stream):
+                lost.zero_()
+            for c, (pk, n, seq0) in enumerate(cl):
+                if ev_base is not None:
+                    ev_c0[ev_base + c].record(stream)
+                xe.xe_correlate_packets(pk, n, stride, seq0, GROUPS_PER_STREAM, sg, vis, c > 0, filled, lost,
+                                        stats, ws, stream=stream)
+                if ev_base is not None:
+                    ev_c1[ev_base + c].record(stream)
+            xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=stream)
+        return step, len(cl)
+
+    step, n_calls = make_step(G)
+    launches_per_step = n_calls * 4 + 1           # per call: init, claim, tally, correlation; + normalise
 
     for _ in range(args.warmup):
         step()
@@ -324,12 +357,12 @@ def run_xe(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for k in range(args.steps):
-            step(ev_base=k * FR)
+            step(ev_base=k * n_calls)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
-    corr_ms = [ev_c0[k].elapsed_time(ev_c1[k]) for k in range(n_ev)]
+    corr_ms = [ev_c0[k].elapsed_time(ev_c1[k]) for k in range(n_calls * args.steps)]
     ms = e0.elapsed_time(e1) / args.steps
     if dist:
         t = torch.tensor([ms], device=dev)
@@ -360,7 +393,27 @@ def run_xe(args):
     except Exception as exc:  # capture is optional for the metric; report why it failed
         print(f"[bench] graph capture failed: {exc}", file=sys.stderr)
 
-    # end to end through host buffers: pinned packets -> H2D per frame -> same calls -> D2H of result
+    # the same integration with one call per frame (T = 4096 per call), for comparison
+    per_frame = None
+    if G > 1:
+        step1, n1 = make_step(1)
+        for _ in range(args.warmup):
+            step1()
+        torch.cuda.synchronize(dev)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for k in range(args.steps):
+            step1(ev_base=k * n1)
+        q1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms1 = q0.elapsed_time(q1) / args.steps
+        c1 = statistics.mean(ev_c0[k].elapsed_time(ev_c1[k]) for k in range(n1 * args.steps))
+        per_frame = {"ms_per_step": ms1, "value": cmac_per_frame() * FR / (ms1 / 1e3) * world, "unit": "CMAC/s",
+                     "correlate_ms_per_call": c1, "frames_per_call": 1}
+        print(f"[bench] one call per frame: {ms1:.3f} ms/step, correlate {c1:.4f} ms/launch", file=sys.stderr,
+              flush=True)
+
+    # end to end through host buffers: pinned packets -> H2D per call -> same calls -> D2H of result
     e2e = run_e2e(xe, torch, dev, pkts, counts, stride, args)
     del pkts
     torch.cuda.empty_cache()
@@ -380,7 +433,7 @@ def run_xe(args):
     pk, how = peaks()
     peak_tflops = 2.0 * pk["bf16_tflops_sustained"]      # FP8 dense = 2 x bf16 (nominal ratio)
     corr_avg_ms = statistics.mean(corr_ms)
-    achieved = cmac_per_frame() * 8 / (corr_avg_ms / 1e3) / 1e12
+    achieved = cmac_per_frame() * G * 8 / (corr_avg_ms / 1e3) / 1e12
     traffic = load_traffic()
     line = {
         "metric": METRIC, "value": value, "unit": "CMAC/s", "n_gpus": world, "steps": args.steps,
@@ -390,11 +443,12 @@ def run_xe(args):
         "realtime_factor": FR * T / SAMPLE_RATE / (ms / 1e3),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "xe_correlate_packets per frame (index kernels + packet-mode CTA-pair tcgen05 "
-                               "correlation), 8 int ops per CMAC, timed by CUDA events around each call",
+                     "kernel": f"xe_correlate_packets over {G} frame(s) per call (index kernels + packet-mode "
+                               "CTA-pair tcgen05 correlation), 8 int ops per CMAC, timed by CUDA events around each call",
                      "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
         "gpu_launches": launches_per_step * args.steps,
         "graph_ms_per_step": graph_ms,
+        "one_call_per_frame": per_frame,
         "clocks": clocks,
         "e2e": e2e,
         "serving": serving,
@@ -425,21 +479,22 @@ def load_traffic():
 
 
 def run_e2e(xe, torch, dev, pkts, counts, stride, args):
-    """Same integration through host buffers: each frame's packets are copied from pinned host memory
-    (a ring of 4 distinct frames) on a copy stream, double-buffered against compute; the normalised
-    matrix is copied back at the end of every step."""
-    N, F, T, FR = N_INPUTS, N_CHAN, N_TIME, args.frames
-    s = xe.Shape(N, F, T)
-    ring = [pkts[k].cpu().pin_memory() for k in range(min(4, FR))]
-    rcount = [counts[k] for k in range(len(ring))]
-    dbuf = [torch.empty((max(rcount), stride), dtype=torch.uint8, device=dev) for _ in range(2)]
-    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
+    """Same integration through host buffers: the packets of G consecutive frames (one call) sit in
+    pinned host memory; every call copies them to the device on a copy stream, double-buffered
+    against compute, and correlates them (each call re-integrates those frames, sequence numbers
+    as in the packets); the normalised matrix is copied back at the end of every step."""
+    N, F, T, FR, G = N_INPUTS, N_CHAN, N_TIME, args.frames, args.frames_per_call
+    sg = xe.Shape(N, F, G * T)
+    n = sum(counts[:G])
+    ring = pkts[0].as_strided((n, stride), (stride, 1)).cpu().pin_memory()
+    dbuf = [torch.empty((n, stride), dtype=torch.uint8, device=dev) for _ in range(2)]
+    filled = torch.empty((G * T // 4, F // 8), dtype=torch.uint8, device=dev)
     lost = torch.zeros(F, dtype=torch.int32, device=dev)
     stats = torch.zeros(5, dtype=torch.int32, device=dev)
     vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
     out = torch.empty((F, npairs(N), 2), dtype=torch.float32, device=dev)
     host_out = torch.empty(out.shape, dtype=torch.float32).pin_memory()
-    ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device=dev)
+    ws = torch.empty(xe.xe_correlate_packets_workspace_size(sg), dtype=torch.uint8, device=dev)
     comp = torch.cuda.Stream(device=dev)
     copy = torch.cuda.Stream(device=dev)
     h2d_done = [torch.cuda.Event() for _ in range(2)]
@@ -448,16 +503,15 @@ def run_e2e(xe, torch, dev, pkts, counts, stride, args):
     def one_step():
         with torch.cuda.stream(comp):
             lost.zero_()
-        for k in range(FR):
-            b = k % 2
-            src = ring[k % len(ring)]
+        for c in range(FR // G):
+            b = c % 2
             with torch.cuda.stream(copy):
                 copy.wait_event(used[b])
-                dbuf[b][:src.shape[0]].copy_(src, non_blocking=True)
+                dbuf[b].copy_(ring, non_blocking=True)
                 h2d_done[b].record(copy)
             comp.wait_event(h2d_done[b])
-            xe.xe_correlate_packets(dbuf[b], rcount[k % len(ring)], stride, k * T // 4, GROUPS_PER_STREAM, s,
-                                    vis, k > 0, filled, lost, stats, ws, stream=comp)
+            xe.xe_correlate_packets(dbuf[b], n, stride, 0, GROUPS_PER_STREAM, sg, vis, c > 0, filled, lost, stats, ws,
+                                    stream=comp)
             used[b].record(comp)
         xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=comp)
         with torch.cuda.stream(comp):
@@ -472,10 +526,10 @@ def run_e2e(xe, torch, dev, pkts, counts, stride, args):
         one_step()
         comp.synchronize()
     dt = (time.perf_counter() - t0) / steps
-    h2d = sum(ring[k % len(ring)].numel() for k in range(FR))
+    h2d = ring.numel() * (FR // G)
     return {"value": cmac_per_frame() * FR / dt, "unit": "CMAC/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(out.numel() * 4), "ms_per_step": dt * 1e3,
-            "realtime_factor": FR * T / SAMPLE_RATE / dt}
+            "realtime_factor": FR * T / SAMPLE_RATE / dt, "frames_per_call": G}
 
 
 # ----------------------------------------------------------------------------- configurations 1, 2, 4
@@ -651,6 +705,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--frames", type=int, default=N_FRAMES)
+    ap.add_argument("--frames-per-call", type=int, default=8,
+                    help="consecutive frames correlated by one call (T = 4096 x this <= 32768: the accumulator "
+                         "stays in tensor memory across them)")
     ap.add_argument("--impl", choices=["xe", "reference"], default="xe")
     ap.add_argument("--no-serving", action="store_true", help="skip the configuration-5 serving run")
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=3,
