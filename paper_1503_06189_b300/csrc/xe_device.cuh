@@ -304,23 +304,25 @@ __device__ __forceinline__ uint32_t nibbles_to_e5m2(uint32_t lo_nibbles) {
 // half-precision lane, (x & 0x000F) ^ 0x6408 has the bits of 1024 + (im ^ 8) = 1032 + im and
 // (x & 0x00F0) ^ 0x6480 those of 1024 + 16 (re ^ 8) = 1152 + 16 re; subtracting 1032 resp. 1152 is
 // exact and leaves im resp. 16 re, whose low bytes are zero, so their high bytes are the E5M2 codes.
-// Four logic operations (the ALU pipe), three integer multiply-highs (x >> 8 and the two byte
-// compactions, on the FMA pipe) and four half2 subtractions for eight codes.
+// One shift and four three-input logic operations with both constants as immediates (written out:
+// left to the compiler the mask-and-flip took more instructions), four half2 subtractions and two
+// byte permutes for eight codes.
 __device__ __forceinline__ void expand4_e5m2(uint32_t x, uint32_t &wre, uint32_t &wim) {
-    const uint32_t x8 = __umulhi(x, 1u << 24);
-    uint32_t im02 = (x & 0x000F000Fu) ^ 0x64086408u;
-    uint32_t im13 = (x8 & 0x000F000Fu) ^ 0x64086408u;
-    uint32_t re02 = (x & 0x00F000F0u) ^ 0x64806480u;
-    uint32_t re13 = (x8 & 0x00F000F0u) ^ 0x64806480u;
+    uint32_t x8, im02, im13, re02, re13;
+    asm("shr.b32 %0, %1, 8;" : "=r"(x8) : "r"(x));
+    // lut 0x6A: (a & b) ^ c
+    asm("lop3.b32 %0, %1, 0x000F000F, 0x64086408, 0x6A;" : "=r"(im02) : "r"(x));
+    asm("lop3.b32 %0, %1, 0x000F000F, 0x64086408, 0x6A;" : "=r"(im13) : "r"(x8));
+    asm("lop3.b32 %0, %1, 0x00F000F0, 0x64806480, 0x6A;" : "=r"(re02) : "r"(x));
+    asm("lop3.b32 %0, %1, 0x00F000F0, 0x64806480, 0x6A;" : "=r"(re13) : "r"(x8));
     const uint32_t k_im = 0x64086408u, k_re = 0x64806480u;
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(im02) : "r"(k_im));
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(im13) : "r"(k_im));
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re02) : "r"(k_re));
     asm("sub.rn.f16x2 %0, %0, %1;" : "+r"(re13) : "r"(k_re));
-    // codes sit in bytes 1 and 3 of each word; (w02 >> 8) | w13 compacts them, and as the bytes do
-    // not overlap this is hi(w02 * 2^24) + w13: one multiply-add on the FMA pipe, not a byte permute
-    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(wre) : "r"(re02), "r"(1u << 24), "r"(re13));
-    asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(wim) : "r"(im02), "r"(1u << 24), "r"(im13));
+    // the codes sit in bytes 1 and 3 of each word: (w02.b1, w13.b1, w02.b3, w13.b3)
+    wre = __byte_perm(re02, re13, 0x7351);
+    wim = __byte_perm(im02, im13, 0x7351);
 }
 
 // 16 packed samples -> 32 E5M2 codes in groups of four inputs: (16 re_0..16 re_3, im_0..im_3,
