@@ -1141,12 +1141,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             ld.next(p, n_pairs, rank, t_row, c);
         };
         uint32_t os = 0, oph = 0;
-        // load the stage the rotation assigns to lb, look up the packets of lb's next stage, then
-        // convert stage i from cb
+        // look up the packets of lb's next stage, load the stage the rotation assigns to lb, then
+        // convert stage i from cb. The lookup goes first into a register of its own: issued after
+        // the sample loads into the owner register their shuffles read, it measured 8 % slower
         auto step = [&](Buf &lb, Buf &cb) -> bool {
             if (cb.nb == 0) return false;
+            uint32_t nown[kOwn];
+#pragma unroll
+            for (int q = 0; q < kOwn; ++q) nown[q] = lb.own[q];
+            if constexpr (kPackets) {
+                if (ow.valid(p)) {
+                    ow.owners(nown);
+                    ow.next(p, n_pairs, rank, t_row, c);
+                }
+            }
             issue(lb);
-            next_owners(lb);
+#pragma unroll
+            for (int q = 0; q < kOwn; ++q) lb.own[q] = nown[q];
             if (!wait(&op_empty[os], oph ^ 1)) return false;
             const uint32_t op = op_base + os * op_stage_bytes;
 #pragma unroll
