@@ -64,6 +64,7 @@ struct Job {                 // 128-byte aligned through its CUtensorMap
     int32_t nb;              // 128-row operand blocks (R / 128)
     int32_t strips;          // work items per channel
     int32_t k_tiles;         // ceil(T / samples per stage)
+    int32_t k_tiles_wide;    // packet mode: ceil(T / (2 x samples per stage)) (wide stages); else k_tiles
     int32_t item_begin;      // first global work-item index of this job
     int32_t pw;              // fused: bytes per packed row in shared memory (min(64, N))
     int32_t max_strip;       // tiles per work item along a row (1..4) for this job
@@ -73,6 +74,8 @@ struct Job {                 // 128-byte aligned through its CUtensorMap
 struct Params {
     Job jobs[XE_MAX_JOBS];
     int32_t n_jobs, n_items, k_flush_tiles;
+    int32_t k_flush_tiles_wide;   // drain interval in wide stages (packet mode), else k_flush_tiles
+    int32_t wide_diag;            // 1: single diagonal items run in wide stages (packet mode)
     int32_t op_stages, pk_stages, slots, n_acc;
     int *status;
     int *counter;            // work-item counter, zero at launch
@@ -706,6 +709,19 @@ __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &jo
     decode_pair_item(p, g, job, f, R, C, dbl);
 }
 
+// Packet mode runs a single diagonal block (R, R) in wide stages of 2 kKt samples: samples
+// t0 .. t0 + kKt - 1 of block R in the A slot and t0 + kKt .. t0 + 2 kKt - 1 in the B slot, 8 MMAs
+// per stage with both operands from one slot. Its converters fill both slots as for a double, so
+// the per-stage cost (packet lookups, gather issue, hand-off) is paid once per 2 kKt samples.
+__device__ __forceinline__ bool item_wide(const Params &p, int R, int C, bool dbl) {
+    return p.wide_diag && R == C && !dbl;
+}
+// stages of an item and its drain interval in stages
+__device__ __forceinline__ void item_stages(const Params &p, const Job &jb, bool wide, int &k_tiles, int &flush) {
+    k_tiles = wide ? jb.k_tiles_wide : jb.k_tiles;
+    flush = wide ? p.k_flush_tiles_wide : p.k_flush_tiles;
+}
+
 // Walks the (item, k-tile) stages of one pair in order (forwarder and L2 prefetch).
 struct PairCursor {
     int g, kt, job, f, R, C, k_tiles;
@@ -715,8 +731,9 @@ struct PairCursor {
         if (g < p.n_items) load(p);
     }
     __device__ __forceinline__ void load(const Params &p) {
-        decode_pair_item(p, g, job, f, R, C);
-        k_tiles = p.jobs[job].k_tiles;
+        bool dbl;
+        decode_pair_item(p, g, job, f, R, C, dbl);
+        k_tiles = item_wide(p, R, C, dbl) ? p.jobs[job].k_tiles_wide : p.jobs[job].k_tiles;
     }
     __device__ __forceinline__ bool valid(const Params &p) const { return g < p.n_items; }
     __device__ __forceinline__ void next(const Params &p, int n_pairs) {
@@ -742,8 +759,10 @@ template <bool kPackets>
 struct PairLoader {
     using S = PairShape<kPackets>;
     static constexpr int kOwn = S::kKt / 4 / 32;          // owner loads per lane and stage
+    static constexpr int kOwnMax = kPackets ? 2 * kOwn : 1;   // a wide stage looks up twice as many
     int g, kt, k_tiles, nblk, t_left;         // t_left = T - (kt * S::kKt + t_row)
     bool va, vb;                              // columns of A / B inside the frame
+    bool wide;                                // packet mode: a wide stage (B rows = the next kKt samples)
     const uint8_t *pa, *pb;                   // frame: sample kt * S::kKt + t_row; packets: in packet 0
     int64_t step, rstep;                      // frame: bytes per stage / between a thread's rows
     const uint32_t *own;                      // packets: owner entry of slot kt * S::kKt / 4 + lane
@@ -752,12 +771,14 @@ struct PairLoader {
 
     __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
         int job, f, R, C;
-        decode_pair_item(p, g, job, f, R, C);
+        bool dbl;
+        decode_pair_item(p, g, job, f, R, C, dbl);
         const Job &jb = p.jobs[job];
         const int N = jb.n_inputs, F = jb.n_chan;
         kt = 0;
-        k_tiles = jb.k_tiles;
-        nblk = R == C ? 1 : 2;
+        wide = kPackets && item_wide(p, R, C, dbl);
+        k_tiles = wide ? jb.k_tiles_wide : jb.k_tiles;
+        nblk = R == C && !wide ? 1 : 2;
         t_left = jb.n_time - t_row;
         const int ca = (2 * R + (int)rank) * 64 + 16 * c, cb = (2 * C + (int)rank) * 64 + 16 * c;
         va = ca < N;
@@ -785,8 +806,8 @@ struct PairLoader {
     __device__ __forceinline__ void next(const Params &p, int n_pairs, uint32_t rank, int t_row, int c) {
         t_left -= S::kKt;
         if constexpr (kPackets) {
-            own += S::kKt / 4;
-            s_left -= S::kKt / 4;
+            own += (wide ? 2 : 1) * (S::kKt / 4);
+            s_left -= (wide ? 2 : 1) * (S::kKt / 4);
         } else {
             pa += step;
             pb += step;
@@ -795,32 +816,35 @@ struct PairLoader {
         g += n_pairs;
         if (g < p.n_items) begin_item(p, rank, t_row, c);
     }
-    // packets: the packets of slots lane, lane + 32, ... of the current stage
-    __device__ __forceinline__ void owners(uint32_t (&o)[kOwn > 0 ? kOwn : 1]) const {
+    // packets: the packets of slots lane, lane + 32, ... of the current stage (a wide stage: then
+    // those of slots kKt / 4 + lane, ... in o[kOwn ..])
+    __device__ __forceinline__ void owners(uint32_t (&o)[kOwnMax]) const {
 #pragma unroll
-        for (int q = 0; q < kOwn; ++q) {
+        for (int q = 0; q < kOwnMax; ++q) {
             o[q] = kNoPacket;
             if constexpr (kPackets) {
-                if (s_left > 32 * q) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[q]) : "l"(own + 32 * q));
+                if ((q < kOwn || wide) && s_left > 32 * q)
+                    asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[q]) : "l"(own + 32 * q));
             }
         }
     }
-    // the current stage's samples of this thread (o[r]: the packet of row r, packet mode)
-    __device__ __forceinline__ void load(const uint32_t (&o)[S::kRows], uint4 (&a)[S::kRows], uint4 (&b)[S::kRows]) const {
+    // the current stage's samples of this thread (packet mode: o[r] / ob[r] the packet of row r of
+    // the A / B slot; ob = o except in wide stages)
+    __device__ __forceinline__ void load(const uint32_t (&o)[S::kRows], const uint32_t (&ob)[S::kRows],
+                                         uint4 (&a)[S::kRows], uint4 (&b)[S::kRows]) const {
         const uint4 z = make_uint4(0, 0, 0, 0);
 #pragma unroll
         for (int r = 0; r < S::kRows; ++r) {
-            bool ok;
-            int64_t off;
             if constexpr (kPackets) {
-                ok = o[r] != kNoPacket;
-                off = (int64_t)o[r] * pstride;
+                const bool ok = o[r] != kNoPacket, okb = ob[r] != kNoPacket;
+                a[r] = ok && va ? dev::ld_stream_16(pa + (int64_t)o[r] * pstride) : z;
+                b[r] = okb && vb ? dev::ld_stream_16(pb + (int64_t)ob[r] * pstride) : z;
             } else {
-                ok = t_left > r * S::kRowStep;
-                off = r * rstep;
+                const bool ok = t_left > r * S::kRowStep;
+                const int64_t off = r * rstep;
+                a[r] = ok && va ? dev::ld_stream_16(pa + off) : z;
+                b[r] = ok && vb ? dev::ld_stream_16(pb + off) : z;
             }
-            a[r] = ok && va ? dev::ld_stream_16(pa + off) : z;
-            b[r] = ok && vb ? dev::ld_stream_16(pb + off) : z;
         }
     }
 };
@@ -936,7 +960,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 bool dbl;
                 decode_pair_item(p, g, job, f, R, C, dbl);
                 dbl = kPackets && dbl;           // frame mode never runs doubles
-                for (int k0 = 0; k0 < p.jobs[job].k_tiles && ok; k0 += p.k_flush_tiles) {
+                int kt_n, fl;
+                item_stages(p, p.jobs[job], kPackets && item_wide(p, R, C, dbl), kt_n, fl);
+                for (int k0 = 0; k0 < kt_n && ok; k0 += fl) {
                     for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {   // a double fills both halves
                         if (*abort_flag || !wait(&epi_done[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
                         dev::mbar_arrive_remote(&acc_empty[acc], 0);
@@ -959,11 +985,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 dbl = kPackets && dbl;           // frame mode never runs doubles
                 const Job &jb = p.jobs[job];
                 // a single block multiplies A by B (B = A on the diagonal) into half acc; a double also
-                // multiplies A by A into half acc and A by B into the other half
+                // multiplies A by A into half acc and A by B into the other half; a wide stage
+                // multiplies each slot by itself into half acc
+                const bool wide = kPackets && item_wide(p, R, C, dbl);
                 const uint32_t b_slot = R == C ? 0u : 1u;
                 const uint32_t acc2 = acc ^ 1u;
-                for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles) {
-                    const int k1 = min(jb.k_tiles, k0 + p.k_flush_tiles);
+                int kt_n, fl;
+                item_stages(p, jb, wide, kt_n, fl);
+                for (int k0 = 0; k0 < kt_n && ok; k0 += fl) {
+                    const int k1 = min(kt_n, k0 + fl);
                     if (*abort_flag || !wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u)) { ok = false; break; }
                     if (dbl && !wait(&acc_empty[acc2], ((acc_ph >> acc2) & 1u) ^ 1u)) { ok = false; break; }
                     dev::tc_fence_after();
@@ -979,6 +1009,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                             if (dbl) {
                                 dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, ad, idesc, accum);
                                 dev::mma_f8f6f4_pair(tmem + acc2 * 256u, ad, bd, idesc, accum);
+                            } else if (wide) {
+                                const uint64_t ad1 = dev::sdesc_mn_sw128(sb + kOpSlotBytes + kk * 4096, kOpSlotBytes);
+                                dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, ad, idesc, accum);
+                                dev::mma_f8f6f4_pair(tmem + acc * 256u, ad1, ad1, idesc, 1u);
                             } else {
                                 dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, bd, idesc, accum);
                             }
@@ -1038,7 +1072,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                     }
                 }
             }
-            for (int k0 = 0; k0 < jb.k_tiles && ok; k0 += p.k_flush_tiles)
+            int kt_n, fl;
+            item_stages(p, jb, kPackets && item_wide(p, R, C_item, dbl), kt_n, fl);
+            for (int k0 = 0; k0 < kt_n && ok; k0 += fl)
             for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {        // a double: block (R, R), then (R, R + 1)
                 const int C = dbl ? R + sub : C_item;
                 const int cb0 = 2 * C;
@@ -1100,7 +1136,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
                          ::"r"(slot + dst1), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
         };
-        constexpr int kOwn = PairLoader<kPackets>::kOwn > 0 ? PairLoader<kPackets>::kOwn : 1;
+        constexpr int kOwn = PairLoader<kPackets>::kOwnMax;
         struct Buf {
             uint4 a[S::kRows], b[S::kRows];
             uint32_t own[kOwn];                       // packets of the stage this buffer receives next
@@ -1125,18 +1161,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 b.nb = 0;
                 return;
             }
-            uint32_t o[S::kRows];
+            uint32_t o[S::kRows], ob[S::kRows];
 #pragma unroll
             for (int r = 0; r < S::kRows; ++r) {
-                o[r] = 0;
+                o[r] = ob[r] = 0;
                 if constexpr (kPackets) {
                     // slot (r kRowStep + t_row) / 4 of the stage: register (r kRowStep / 4) / 32,
-                    // lane (r kRowStep / 4) % 32 + t_row / 4 (t_row / 4 < kRowStep / 4 <= 32)
+                    // lane (r kRowStep / 4) % 32 + t_row / 4 (t_row / 4 < kRowStep / 4 <= 32); a wide
+                    // stage's B rows: the same slot kKt / 4 further on (registers kOwn / 2 ..)
+                    constexpr int kHalf = PairLoader<kPackets>::kOwn;
                     const int s0 = r * (S::kRowStep / 4);
                     o[r] = __shfl_sync(0xffffffffu, b.own[s0 / 32], s0 % 32 + (t_row >> 2));
+                    ob[r] = o[r];
+                    if (ld.wide) ob[r] = __shfl_sync(0xffffffffu, b.own[kHalf + s0 / 32], s0 % 32 + (t_row >> 2));
                 }
             }
-            ld.load(o, b.a, b.b);
+            ld.load(o, ob, b.a, b.b);
             b.nb = ld.nblk;
             ld.next(p, n_pairs, rank, t_row, c);
         };
@@ -1449,6 +1489,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             d.strips = strips_per_channel(g.nb, d.max_strip);
         }
         d.k_tiles = (int)((s.n_time + kt_of(engine, pk != nullptr) - 1) / kt_of(engine, pk != nullptr));
+        // packet mode: single diagonal blocks run in stages of twice the samples
+        const int kt_wide = 2 * kt_of(engine, pk != nullptr);
+        d.k_tiles_wide = engine == kFusedPair && pk ? (int)((s.n_time + kt_wide - 1) / kt_wide) : d.k_tiles;
         d.item_begin = items;
         const int64_t add = (int64_t)d.strips * s.n_chan;
         if (items + add > INT32_MAX / 2) return XE_EINVAL;
@@ -1459,6 +1502,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     hp.n_items = items;
     // drain at least once per stage; a stage (<= 256 samples) never exceeds the exactness bound
     hp.k_flush_tiles = std::max(1, tune.k_flush / kt_of(engine, pk != nullptr));
+    // wide stages (2 x 128 samples) stay within the exactness bound like any stage of <= 256 samples
+    hp.wide_diag = engine == kFusedPair && pk ? 1 : 0;
+    hp.k_flush_tiles_wide = hp.wide_diag ? std::max(1, tune.k_flush / (2 * kt_of(engine, true))) : hp.k_flush_tiles;
     hp.slots = ms_max == 1 ? 2 : (ms_max == 2 ? 3 : 4);     // operand blocks per stage for the widest strip
     hp.n_acc = ms_max <= 2 ? 2 : 1;                        // TMEM accumulators (each <= 256 columns)
     hp.status = status;
