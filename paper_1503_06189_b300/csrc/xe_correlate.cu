@@ -62,13 +62,15 @@ struct Job {                 // 128-byte aligned through its CUtensorMap
     uint32_t pkt_stride;     // packet mode: bytes from one packet to the next
     int32_t n_inputs, n_chan, n_time, accumulate;
     int32_t nb;              // 128-row operand blocks (R / 128)
-    int32_t strips;          // work items per channel
+    int32_t strips;          // work items per channel (pair engine, packet mode: per channel pair)
     int32_t k_tiles;         // ceil(T / samples per stage)
     int32_t k_tiles_wide;    // packet mode: ceil(T / (2 x samples per stage)) (wide stages); else k_tiles
     int32_t item_begin;      // first global work-item index of this job
     int32_t pw;              // fused: bytes per packed row in shared memory (min(64, N))
     int32_t max_strip;       // tiles per work item along a row (1..4) for this job
     int32_t doubles;         // pair engine: double items per channel (0: every block a single item)
+    int32_t offdiag;         // pair engine, packet mode: blocks (R, C >= R + 2) per channel
+    int32_t twin;            // pair engine: 1 = packet-mode item layout (doubles, singles, twins)
 };
 
 struct Params {
@@ -657,38 +659,79 @@ struct PairShape {
     static_assert(kRowStep % 8 == 0, "a thread's rows share their 128-byte swizzle phase");
 };
 constexpr int kPairMaxStages = 6;
+// Packet mode: integrations of at least this many samples run the twin layout (see decode_pair_item)
+constexpr int kTwinMinTime = 16384;
 constexpr int kPairPrefetch = 4;              // L2 prefetch distance in stages
 
-// Work items of one job with doubles (packet mode), channel by channel: the channel's doubles, then
-// its single blocks: 2 items per channel instead of 3 at N = 256, 25 % fewer conversions and sample
-// gathers. Pairs take items pair, pair + pairs, ...; the launch uses an odd number of pairs, so a
-// pair alternates between doubles and singles. (Frame mode, with 256-sample stages, runs every block
-// as its own item: doubles make its stages MMA-bound, 0.80 -> 0.84 ms.) A double is the diagonal block
-// (R, R) together with its right neighbour (R, R + 1), R < S2 - 1: both multiply the same A block, so
-// they are computed together into the two TMEM halves from one converted operand stage (A, B =
-// block R + 1). Singles are the blocks (R, C), C >= R + 2, and the last diagonal block (S2 - 1,
-// S2 - 1). Returns C = R + 1 for a double (the block loaded as B).
-__device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C, bool &dbl) {
+// Work items of a frame-mode job: every 256x256 block (R, C >= R) of every channel its own item.
+// Work items of a packet-mode job, by pairs of channels (2c, 2c + 1), which share a packet group:
+// - each channel's doubles: the diagonal block (R, R) together with its right neighbour (R, R + 1),
+//   R < S2 - 1, computed into the two TMEM halves from one operand stage (A = block R, B = block
+//   R + 1);
+// - its singles (R, C >= R + 2);
+// - then one twin: the last diagonal block (S2 - 1, S2 - 1) of both channels, channel 2c's block in
+//   the A slot and channel 2c + 1's (N bytes further into the same packets) in the B slot, each
+//   multiplied by itself into its own TMEM half.
+// At N = 256 a channel pair is two doubles and a twin, all with 8 MMAs and four converted blocks
+// per stage: the items of neighbouring pairs run in lockstep and share their packets in L2. An odd
+// last channel ends with its diagonal block as a single (a wide one, 2 x kKt samples per stage).
+// Pairs take items pair, pair + pairs, ...; the launch uses an odd number of pairs. (Frame mode, with
+// 256-sample stages, runs every block as its own item: doubles make its stages MMA-bound, 0.80 ->
+// 0.84 ms.) dbl: the item fills both TMEM halves (a double or a twin); C = R + 1 for a double (the
+// block loaded as B), C = R for a twin.
+__device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C, bool &dbl,
+                                                 bool &twin) {
     int j = 0;
     while (j + 1 < p.n_jobs && g >= p.jobs[j + 1].item_begin) ++j;
     const Job &jb = p.jobs[j];
     int l = g - jb.item_begin;
     job = j;
     const int S2 = jb.nb;                     // 256-row super-blocks
-    const int D = jb.doubles;                 // doubles per channel: S2 - 1, or 0 (all singles)
-    if (D == 0) {                             // every block (R, C >= R) its own item
+    twin = false;
+    dbl = false;
+    int q;
+    if (!jb.twin) {
         f = l / jb.strips;
-        int q = l % jb.strips;
-        dbl = false;
-        for (R = 0; R < S2; ++R) {
-            if (q < S2 - R) break;
-            q -= S2 - R;
+        q = l % jb.strips;
+        if (jb.doubles == 0) {                // frame mode: every block (R, C >= R) its own item
+            for (R = 0; R < S2; ++R) {
+                if (q < S2 - R) break;
+                q -= S2 - R;
+            }
+            C = R + q;
+            return;
         }
-        C = R + q;
+        if (q < jb.doubles) {                 // packet mode, channel by channel: doubles,
+            R = q;
+            C = R + 1;
+            dbl = true;
+            return;
+        }
+        q -= jb.doubles;                      // then singles, the last diagonal (wide) at the end
+        for (R = 0; R < S2 - 1; ++R) {
+            if (q < S2 - R - 2) break;
+            q -= S2 - R - 2;
+        }
+        C = R < S2 - 1 ? R + 2 + q : R;
         return;
     }
-    f = l / jb.strips;
-    int q = l % jb.strips;
+    const int D = jb.doubles, per_ch = jb.doubles + jb.offdiag;
+    const int per2 = jb.strips;               // 2 per_ch + 1 items per channel pair
+    const int cp = l / per2;
+    q = l % per2;
+    if (cp < jb.n_chan / 2) {
+        if (q == per2 - 1) {                  // the twin of channels 2 cp and 2 cp + 1
+            f = 2 * cp;
+            R = C = S2 - 1;
+            dbl = twin = true;
+            return;
+        }
+        f = 2 * cp + q / per_ch;              // q < 2 per_ch, so per_ch > 0 here
+        q %= per_ch;
+    } else {                                  // the odd last channel: doubles, singles, its diagonal
+        f = jb.n_chan - 1;
+        q = l - (jb.n_chan / 2) * per2;
+    }
     if (q < D) {
         R = q;
         C = R + 1;
@@ -696,7 +739,6 @@ __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &jo
         return;
     }
     q -= D;
-    dbl = false;
     for (R = 0; R < S2 - 1; ++R) {
         if (q < S2 - R - 2) break;
         q -= S2 - R - 2;
@@ -705,11 +747,12 @@ __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &jo
 }
 
 __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C) {
-    bool dbl;
-    decode_pair_item(p, g, job, f, R, C, dbl);
+    bool dbl, twin;
+    decode_pair_item(p, g, job, f, R, C, dbl, twin);
 }
 
-// Packet mode runs a single diagonal block (R, R) in wide stages of 2 kKt samples: samples
+// Packet mode runs a single diagonal block (R, R) (an odd last channel's) in wide stages of 2 kKt
+// samples: samples
 // t0 .. t0 + kKt - 1 of block R in the A slot and t0 + kKt .. t0 + 2 kKt - 1 in the B slot, 8 MMAs
 // per stage with both operands from one slot. Its converters fill both slots as for a double, so
 // the per-stage cost (packet lookups, gather issue, hand-off) is paid once per 2 kKt samples.
@@ -731,8 +774,8 @@ struct PairCursor {
         if (g < p.n_items) load(p);
     }
     __device__ __forceinline__ void load(const Params &p) {
-        bool dbl;
-        decode_pair_item(p, g, job, f, R, C, dbl);
+        bool dbl, twin;
+        decode_pair_item(p, g, job, f, R, C, dbl, twin);
         k_tiles = item_wide(p, R, C, dbl) ? p.jobs[job].k_tiles_wide : p.jobs[job].k_tiles;
     }
     __device__ __forceinline__ bool valid(const Params &p) const { return g < p.n_items; }
@@ -771,14 +814,15 @@ struct PairLoader {
 
     __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
         int job, f, R, C;
-        bool dbl;
-        decode_pair_item(p, g, job, f, R, C, dbl);
+        bool dbl, twin;
+        decode_pair_item(p, g, job, f, R, C, dbl, twin);
         const Job &jb = p.jobs[job];
         const int N = jb.n_inputs, F = jb.n_chan;
         kt = 0;
         wide = kPackets && item_wide(p, R, C, dbl);
+        twin = kPackets && twin;
         k_tiles = wide ? jb.k_tiles_wide : jb.k_tiles;
-        nblk = R == C && !wide ? 1 : 2;
+        nblk = R == C && !wide && !twin ? 1 : 2;
         t_left = jb.n_time - t_row;
         const int ca = (2 * R + (int)rank) * 64 + 16 * c, cb = (2 * C + (int)rank) * 64 + 16 * c;
         va = ca < N;
@@ -796,7 +840,7 @@ struct PairLoader {
             rstep = (int64_t)S::kRowStep * F * N;
         }
         pa = base + ca;
-        pb = base + cb;
+        pb = base + cb + (twin ? N : 0);      // a twin's B block: channel f + 1, N bytes on
     }
     __device__ __forceinline__ void start(const Params &p, int pair, uint32_t rank, int t_row, int c) {
         g = pair;
@@ -957,9 +1001,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             bool ok = true;
             for (int g = pair; g < p.n_items && ok; g += n_pairs) {
                 int job, f, R, C;
-                bool dbl;
-                decode_pair_item(p, g, job, f, R, C, dbl);
-                dbl = kPackets && dbl;           // frame mode never runs doubles
+                bool dbl, twin;
+                decode_pair_item(p, g, job, f, R, C, dbl, twin);
+                dbl = kPackets && dbl;           // frame mode never runs doubles or twins
                 int kt_n, fl;
                 item_stages(p, p.jobs[job], kPackets && item_wide(p, R, C, dbl), kt_n, fl);
                 for (int k0 = 0; k0 < kt_n && ok; k0 += fl) {
@@ -980,15 +1024,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             bool ok = true;
             for (int g = pair; g < p.n_items && ok; g += n_pairs) {
                 int job, f, R, C;
-                bool dbl;
-                decode_pair_item(p, g, job, f, R, C, dbl);
-                dbl = kPackets && dbl;           // frame mode never runs doubles
+                bool dbl, twin;
+                decode_pair_item(p, g, job, f, R, C, dbl, twin);
+                dbl = kPackets && dbl;           // frame mode never runs doubles or twins
+                twin = kPackets && twin;
                 const Job &jb = p.jobs[job];
-                // a single block multiplies A by B (B = A on the diagonal) into half acc; a double also
-                // multiplies A by A into half acc and A by B into the other half; a wide stage
-                // multiplies each slot by itself into half acc
+                // a single block multiplies A by B (B = A on the diagonal) into half acc; a double
+                // multiplies A by A into half acc and A by B into the other half; a twin A by A and B
+                // by B; a wide stage multiplies each slot by itself into half acc
                 const bool wide = kPackets && item_wide(p, R, C, dbl);
-                const uint32_t b_slot = R == C ? 0u : 1u;
+                const uint32_t b_slot = R == C && !twin ? 0u : 1u;
                 const uint32_t acc2 = acc ^ 1u;
                 int kt_n, fl;
                 item_stages(p, jb, wide, kt_n, fl);
@@ -1008,7 +1053,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                             const uint32_t accum = (kt > k0 || kk > 0) ? 1u : 0u;
                             if (dbl) {
                                 dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, ad, idesc, accum);
-                                dev::mma_f8f6f4_pair(tmem + acc2 * 256u, ad, bd, idesc, accum);
+                                dev::mma_f8f6f4_pair(tmem + acc2 * 256u, twin ? bd : ad, bd, idesc, accum);
                             } else if (wide) {
                                 const uint64_t ad1 = dev::sdesc_mn_sw128(sb + kOpSlotBytes + kk * 4096, kOpSlotBytes);
                                 dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, ad, idesc, accum);
@@ -1046,9 +1091,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         bool ok = true;
         for (int g = pair; g < p.n_items && ok; g += n_pairs) {
             int job, f, R, C_item;
-            bool dbl;
-            decode_pair_item(p, g, job, f, R, C_item, dbl);
-            dbl = kPackets && dbl;               // frame mode never runs doubles
+            bool dbl, twin;
+            decode_pair_item(p, g, job, f, R, C_item, dbl, twin);
+            dbl = kPackets && dbl;               // frame mode never runs doubles or twins
+            twin = kPackets && twin;
             const Job &jb = p.jobs[job];
             const int N = jb.n_inputs;
             const int rb = 2 * R + (int)rank;
@@ -1062,13 +1108,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 // drain of a half holds up the tensor core, a double item filling all of TMEM);
                 // frame mode measured slower with the prefetch
                 for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {
-                    const int jc = (2 * (dbl ? R + sub : C_item) * kBlk) / 2 + (im_row ? 8 : 0);
+                    const int jc = (2 * (dbl && !twin ? R + sub : C_item) * kBlk) / 2 + (im_row ? 8 : 0);
+                    const int32_t *vis_s = vis_f + (twin ? (size_t)sub * (size_t)npairs(N) * 2 : 0);
 #pragma unroll 1
                     for (int ck = 0; ck < n_chunks; ++ck) {
                         const int j0 = max(jc + 16 * ck, i), j1 = min(jc + 16 * ck + 7, N - 1);
                         if (j0 > j1) continue;
-                        dev::prefetch_l2(vis_f + 2 * (prow + j0));
-                        dev::prefetch_l2(vis_f + 2 * (prow + j1));
+                        dev::prefetch_l2(vis_s + 2 * (prow + j0));
+                        dev::prefetch_l2(vis_s + 2 * (prow + j1));
                     }
                 }
             }
@@ -1076,8 +1123,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             item_stages(p, jb, kPackets && item_wide(p, R, C_item, dbl), kt_n, fl);
             for (int k0 = 0; k0 < kt_n && ok; k0 += fl)
             for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {        // a double: block (R, R), then (R, R + 1)
-                const int C = dbl ? R + sub : C_item;
+                const int C = dbl && !twin ? R + sub : C_item;      // a twin: (R, R) of channel f, then f + 1
                 const int cb0 = 2 * C;
+                int32_t *vis_s = vis_f + (twin ? (size_t)sub * (size_t)npairs(N) * 2 : 0);
                 if (*abort_flag || !wait(&acc_full[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
                 dev::tc_fence_after();
                 const bool add = jb.accumulate || k0 > 0;
@@ -1085,7 +1133,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 auto jb_of = [&](int ck) { return (cb0 * kBlk + ck * 32) / 2 + (im_row ? 8 : 0); };
                 int2 old[8], nxt[8];
                 int ck = half;
-                if (add && ck < n_chunks) load_old(vis_f, prow, i, jb_of(ck), N, i_ok, old);
+                if (add && ck < n_chunks) load_old(vis_s, prow, i, jb_of(ck), N, i_ok, old);
                 else {
 #pragma unroll
                     for (int k = 0; k < 8; ++k) old[k] = make_int2(0, 0);
@@ -1097,17 +1145,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 for (; ck < n_chunks; ck += kPerQuarter) {
                     const bool more = ck + kPerQuarter < n_chunks;
                     if constexpr (kPackets) {
-                        if (add && more) load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, nxt);
+                        if (add && more) load_old(vis_s, prow, i, jb_of(ck + kPerQuarter), N, i_ok, nxt);
                     }
                     int vr[8], vi[8];
                     combine_chunk<true>(tb + ck * 32, im_row, vr, vi);
-                    store_vis(vis_f, prow, i, jb_of(ck), N, i_ok, vr, vi, old);
+                    store_vis(vis_s, prow, i, jb_of(ck), N, i_ok, vr, vi, old);
                     if (add && more) {
                         if constexpr (kPackets) {
 #pragma unroll
                             for (int k = 0; k < 8; ++k) old[k] = nxt[k];
                         } else {
-                            load_old(vis_f, prow, i, jb_of(ck + kPerQuarter), N, i_ok, old);
+                            load_old(vis_s, prow, i, jb_of(ck + kPerQuarter), N, i_ok, old);
                         }
                     }
                 }
@@ -1471,14 +1519,29 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         d.n_chan = s.n_chan;
         d.n_time = s.n_time;
         d.accumulate = jobs[j].accumulate ? 1 : 0;
+        int64_t job_items = 0;
         if (engine == kFusedPair) {             // 256x256 blocks on or above the diagonal
             d.nb = (g.nb + 1) / 2;
-            if (pk) {                           // S2 - 1 doubles and (S2 - 1)(S2 - 2) / 2 + 1 singles
+            if (pk) {
+                // per channel S2 - 1 doubles and (S2 - 1)(S2 - 2) / 2 singles; then long
+                // integrations take the last diagonal blocks of channel pairs as twins (an odd last
+                // channel keeps its diagonal single), short ones each channel's as a wide single
                 d.doubles = d.nb - 1;
-                d.strips = (d.nb - 1) + (d.nb - 1) * (d.nb - 2) / 2 + 1;
+                d.offdiag = (d.nb - 1) * (d.nb - 2) / 2;
+                d.twin = s.n_time >= kTwinMinTime ? 1 : 0;
+                if (d.twin) {
+                    d.strips = 2 * (d.doubles + d.offdiag) + 1;
+                    job_items = (int64_t)(s.n_chan / 2) * d.strips + (s.n_chan % 2) * (d.doubles + d.offdiag + 1);
+                } else {
+                    d.strips = d.doubles + d.offdiag + 1;
+                    job_items = (int64_t)d.strips * s.n_chan;
+                }
             } else {
                 d.doubles = 0;
+                d.offdiag = 0;
+                d.twin = 0;
                 d.strips = d.nb * (d.nb + 1) / 2;
+                job_items = (int64_t)d.strips * s.n_chan;
             }
             d.max_strip = 2;
         } else {
@@ -1487,15 +1550,15 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             if (d.max_strip > 4) return XE_EINVAL;
             ms_max = std::max(ms_max, d.max_strip);
             d.strips = strips_per_channel(g.nb, d.max_strip);
+            job_items = (int64_t)d.strips * s.n_chan;
         }
         d.k_tiles = (int)((s.n_time + kt_of(engine, pk != nullptr) - 1) / kt_of(engine, pk != nullptr));
         // packet mode: single diagonal blocks run in stages of twice the samples
         const int kt_wide = 2 * kt_of(engine, pk != nullptr);
         d.k_tiles_wide = engine == kFusedPair && pk ? (int)((s.n_time + kt_wide - 1) / kt_wide) : d.k_tiles;
         d.item_begin = items;
-        const int64_t add = (int64_t)d.strips * s.n_chan;
-        if (items + add > INT32_MAX / 2) return XE_EINVAL;
-        items += (int)add;
+        if (items + job_items > INT32_MAX / 2) return XE_EINVAL;
+        items += (int)job_items;
     }
     if (nj == 0) return XE_OK;
     hp.n_jobs = nj;

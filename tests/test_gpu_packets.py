@@ -44,6 +44,11 @@ def _host(t, dtype=None):
     (80, 24, 512, 3, 0.1, 0.1, 0.1),           # ragged input block (N % 64 = 16), three groups
     (192, 16, 1028, 1, 0.5, 0.5, 0.3),         # half-empty second super-block, heavy loss
     (256, 64, 256, 2, 0.02, 0.1, 0.02),        # per-server Pathfinder inputs
+    (512, 8, 256, 1, 0.02, 0.1, 0.02),         # four super-blocks: doubles, off-diagonal singles, twins
+    (640, 16, 132, 2, 0.05, 0.1, 0.05),        # five, the last half empty; ragged time tail
+    # integrations of >= 16384 samples take the twin layout (two channels' last diagonal blocks)
+    (256, 8, 16388, 1, 0.01, 0.05, 0.01),      # two doubles and a twin per channel pair; ragged tail
+    (384, 8, 16384, 1, 0.01, 0.05, 0.01),      # three super-blocks: doubles, a single, a twin
 ])
 def test_packets_match_oracle(N, F, T, gps, p_drop, p_reorder, p_dup):
     fr = synth.signal_frame(N, F, T + 64, 40 + N + T)
