@@ -413,6 +413,8 @@ def run_xe(args):
         print(f"[bench] one call per frame: {ms1:.3f} ms/step, correlate {c1:.4f} ms/launch", file=sys.stderr,
               flush=True)
 
+    baselines = run_engine_baselines(xe, torch, dev)
+
     # end to end through host buffers: pinned packets -> H2D per call -> same calls -> D2H of result
     e2e = run_e2e(xe, torch, dev, pkts, counts, stride, args)
     del pkts
@@ -449,6 +451,7 @@ def run_xe(args):
         "gpu_launches": launches_per_step * args.steps,
         "graph_ms_per_step": graph_ms,
         "one_call_per_frame": per_frame,
+        "engine_baselines": baselines,
         "clocks": clocks,
         "e2e": e2e,
         "serving": serving,
@@ -459,6 +462,37 @@ def run_xe(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def run_engine_baselines(xe, torch, dev, reps: int = 3):
+    """The legacy warp-level engine (mma.sync m16n8k64 s4 on the packed samples) and the default
+    CTA-pair tcgen05 engine on the same assembled full-band frame (N=256, F=1024, T=4096, random
+    bytes), best of `reps` launches each: context for what the tensor-core path buys."""
+    N, F, T = N_INPUTS, N_CHAN, N_TIME
+    g = torch.Generator(device=dev)
+    g.manual_seed(77)
+    frame = torch.randint(0, 256, (T, F, N), generator=g, device=dev, dtype=torch.int32).to(torch.uint8)
+    vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
+    out = {}
+    for name, eng in (("legacy_mma_sync_s4", xe.XE_ENGINE_LEGACY_S4), ("tcgen05_pair", xe.XE_ENGINE_FUSED_PAIR)):
+        tune = dict(engine=eng, max_strip=0, k_flush=0, n_ctas=0)
+        jobs = [(frame, vis, xe.Shape(N, F, T), False)]
+        ws = torch.empty(max(1, xe.xe_correlate_batched_workspace_size(jobs, tune)), dtype=torch.uint8, device=dev)
+        best = None
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            xe.xe_correlate_batched(jobs, ws, tune)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name] = {"ms_per_frame": best, "value": cmac_per_frame() / (best / 1e3), "unit": "CMAC/s"}
+        del ws
+    del frame, vis
+    torch.cuda.empty_cache()
+    out["workload"] = "one assembled full-band frame, N=256, F=1024, T=4096, random bytes, xe_correlate_batched"
+    return out
 
 
 def load_traffic():

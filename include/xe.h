@@ -139,6 +139,10 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
 #define XE_ENGINE_FUSED 2       /* the GEMM loads packed bytes and expands them in shared memory */
 #define XE_ENGINE_UNPACKED_K 3  /* A2 unpack to HBM transposed (K-major), then the GEMM */
 #define XE_ENGINE_FUSED_PAIR 4  /* as FUSED, on CTA pairs: 256x256 blocks with M = 256 pair MMAs */
+#define XE_ENGINE_LEGACY_S4 5   /* baseline, no tcgen05: warp-level mma.sync m16n8k64 with 4-bit signed
+                                   operands straight on the packed samples (three MMAs per tile:
+                                   Re V = A B^T, Im V = 2 A' B'^T - A B'^T with B' nibble-swapped and
+                                   A' the Im nibbles); max_strip, k_flush and n_ctas are ignored */
 
 typedef struct {
     int32_t engine;      /* XE_ENGINE_* */
@@ -166,6 +170,16 @@ typedef struct {
 size_t xe_correlate_workspace_size(xe_shape s);
 int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate, void *ws,
                  size_t ws_bytes, void *stream);
+
+/*
+ * Rate probe of the legacy warp-level integer tensor path (the baseline XE_ENGINE_LEGACY_S4 runs
+ * on): `blocks` CTAs of 256 threads, each warp issuing iters x 8 independent mma.sync with
+ * register operands. kind 0: m16n8k64 s4 x s4 -> s32 (16,384 int ops per instruction); kind 1:
+ * m16n8k32 s8 x s8 -> s32 (8,192). The caller times the launch on `stream`.
+ *   sink   device, int32 [blocks * 256]: written (keeps the results live), values meaningless.
+ * Errors: XE_EINVAL (kind, blocks < 1, iters < 1, sink NULL), XE_ECUDA.
+ */
+int xe_probe_mma_legacy(int32_t kind, int32_t blocks, int32_t iters, int32_t *sink, void *stream);
 
 /* ---------------------------------------------------------------- A6: batched persistent */
 

@@ -20,13 +20,14 @@ XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ENOMEM, XE_ECUDA, XE_ETIMEOUT, XE_EAGAIN = 0,
 XE_MAX_TIME = (1 << 24) - 1
 XE_MAX_JOBS = 64
 XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K, XE_ENGINE_FUSED_PAIR = 0, 1, 2, 3, 4
+XE_ENGINE_LEGACY_S4 = 5
 
 EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",
     "xe_assemble_workspace_size", "xe_assemble", "xe_assemble_noalloc", "xe_unpack", "xe_correlate_workspace_size",
     "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched",
     "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_flag_counts_workspace_size",
-    "xe_flag_counts", "xe_normalize",
+    "xe_flag_counts", "xe_normalize", "xe_probe_mma_legacy",
     "xe_stream_create", "xe_stream_submit", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
     "xe_stream_stats", "xe_stream_destroy",
 ]
@@ -96,6 +97,7 @@ def _load():
     L.xe_version.restype = ctypes.c_int
     L.xe_device_status.argtypes = [ctypes.POINTER(ctypes.c_int), vp]
     L.xe_selftest_timeout.argtypes = [u64, vp]
+    L.xe_probe_mma_legacy.argtypes = [i32, i32, i32, vp, vp]
     L.xe_assemble_workspace_size.restype = sz
     L.xe_assemble_workspace_size.argtypes = [Shape]
     L.xe_assemble.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, vp, vp, vp, sz, vp]
@@ -199,6 +201,11 @@ def xe_device_status(stream=None) -> int:
 
 def xe_selftest_timeout(timeout_ns: int, stream=None):
     _check(_L.xe_selftest_timeout(timeout_ns, _stream(stream)), "xe_selftest_timeout")
+
+
+def xe_probe_mma_legacy(kind: int, blocks: int, iters: int, sink, stream=None):
+    """Rate probe of the legacy mma.sync path: kind 0 = m16n8k64 s4, 1 = m16n8k32 s8."""
+    _check(_L.xe_probe_mma_legacy(kind, blocks, iters, _ptr(sink), _stream(stream)), "xe_probe_mma_legacy")
 
 
 # ----------------------------------------------------------------------------- A1

@@ -64,6 +64,11 @@ struct packet_src {
 int correlate_packets_batched(const xe_job *jobs, const packet_src *src, int n_jobs, void *ws, size_t ws_bytes,
                               cudaStream_t st);
 
+namespace legacy {
+// XE_ENGINE_LEGACY_S4: the jobs (checked by the caller) on the mma.sync 4-bit path, one launch per job.
+int correlate_s4(const xe_job *jobs, int n_jobs, cudaStream_t st);
+}  // namespace legacy
+
 inline bool valid_shape(const xe_shape &s) {
     return s.n_inputs >= 16 && s.n_inputs <= 4096 && s.n_inputs % 16 == 0 && s.n_chan >= 1 &&
            s.n_time >= 0;

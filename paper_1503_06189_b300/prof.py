@@ -22,7 +22,7 @@ import paper_1503_06189_b300 as xe
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["correlate", "assemble", "normalize", "packets", "flags"])
+    ap.add_argument("op", choices=["correlate", "assemble", "normalize", "packets", "flags", "mma_legacy"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--f", type=int, default=128)
     ap.add_argument("--t", type=int, default=4096)
@@ -136,6 +136,22 @@ def main(argv=None):
         best = min(ms[1:] if len(ms) > 1 else ms)
         print(f"flags N={N} F={F} T={T}: best {best:.4f} ms for {pk.numel() / 1e6:.0f} MB of packets, "
               f"{float(np.mean(fl)) * 100:.3f}% of samples flagged", flush=True)
+    elif a.op == "mma_legacy":
+        # rate of the legacy warp-level integer tensor path (what XE_ENGINE_LEGACY_S4 runs on)
+        blocks = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+        sink = torch.empty(blocks * 256, dtype=torch.int32, device=dev)
+        for kind, name, ops in ((0, "m16n8k64 s4", 16384), (1, "m16n8k32 s8", 8192)):
+            iters = 4000
+            xe.xe_probe_mma_legacy(kind, blocks, 10, sink)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            xe.xe_probe_mma_legacy(kind, blocks, iters, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            total = blocks * 8 * iters * 8 * ops
+            print(f"mma.sync {name}: {total / ms / 1e9:.1f} T int-op/s ({blocks} CTAs x 8 warps x {iters} x 8 "
+                  f"instructions in {ms:.3f} ms)", flush=True)
     else:
         lost = torch.zeros(F, dtype=torch.int32, device=dev)
         out = torch.empty((F, P, 2), dtype=torch.float32, device=dev)

@@ -82,6 +82,34 @@ def test_correlate_worst_case_magnitudes():
     assert_vis_equal(X.correlate(fr), want)
 
 
+@pytest.mark.parametrize("engine", [xe.XE_ENGINE_FUSED_PAIR, xe.XE_ENGINE_LEGACY_S4])
+def test_correlate_int32_limit_closed_form(engine):
+    """Every sample -8-8i over the longest integration the int32 output holds (T = 2^24 - 1): each
+    visibility is T (-8-8i)(-8+8i) = 128 T = 2,147,483,520 + 0i, 128 below 2^31 (closed form)."""
+    T, F, N = xe.XE_MAX_TIME, 1, 16
+    frame = torch.full((T, F, N), 0x88, dtype=torch.uint8, device="cuda")
+    (got,) = X.correlate_batched([frame], tune=dict(engine=engine, max_strip=0, k_flush=0, n_ctas=0))
+    g = got.cpu().numpy().astype(np.int64)
+    assert (g[..., 0] == 128 * T).all() and (g[..., 1] == 0).all()
+
+
+def test_legacy_engine_accumulates():
+    """The legacy mma.sync engine adds to the visibilities of an earlier call (Sec. II-B)."""
+    a = synth.signal_frame(96, 3, 700, 11)
+    b = synth.signal_frame(96, 3, 260, 12)
+    va, _ = oracle.correlate(a)
+    vb, _ = oracle.correlate(b)
+    tune = dict(engine=xe.XE_ENGINE_LEGACY_S4, max_strip=0, k_flush=0, n_ctas=0)
+    fa, fb = X.dev(a), X.dev(b)
+    s_a, s_b = xe.Shape(96, 3, 700), xe.Shape(96, 3, 260)
+    vis = torch.full((3, xe.npairs(96), 2), -5, dtype=torch.int32, device="cuda")
+    ws = torch.empty(xe.xe_correlate_batched_workspace_size([(fa, vis, s_a, False)], tune), dtype=torch.uint8,
+                     device="cuda")
+    xe.xe_correlate_batched([(fa, vis, s_a, False)], ws, tune)
+    xe.xe_correlate_batched([(fb, vis, s_b, True)], ws, tune)
+    assert_vis_equal(vis, va + vb)
+
+
 def test_correlate_overflow_bound_rejected():
     s = xe.Shape(16, 1, xe.XE_MAX_TIME + 1)
     vis = torch.zeros((1, xe.npairs(16), 2), dtype=torch.int32, device="cuda")
@@ -108,7 +136,8 @@ def test_correlate_workspace_too_small():
     assert e.value.status == xe.XE_ENOMEM
 
 
-ENGINES = [xe.XE_ENGINE_FUSED, xe.XE_ENGINE_UNPACKED, xe.XE_ENGINE_UNPACKED_K, xe.XE_ENGINE_FUSED_PAIR]
+ENGINES = [xe.XE_ENGINE_FUSED, xe.XE_ENGINE_UNPACKED, xe.XE_ENGINE_UNPACKED_K, xe.XE_ENGINE_FUSED_PAIR,
+           xe.XE_ENGINE_LEGACY_S4]
 
 
 @pytest.mark.parametrize("engine", ENGINES)
