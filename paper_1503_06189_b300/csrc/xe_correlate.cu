@@ -10,7 +10,7 @@
 // tensor memory, and the accumulator is drained to int32 at least every k_flush samples. Only
 // 128x128 tiles of G on or above the block diagonal are computed.
 //
-// Engines (one kernel template, one persistent CTA per SM):
+// Single-CTA engines (one kernel template, one persistent CTA per SM):
 //   UNPACKED_K  A2 unpack writes Y K-major [F][R][ldy]; TMA loads 128x128-byte swizzled tiles.
 //   UNPACKED    A2 unpack writes Y MN-major [F][ldy][R] (an in-order byte expansion of the frame);
 //               TMA loads 128 (t) x 128-byte tiles; MMAs read MN-major operands.
@@ -21,6 +21,10 @@
 // accumulate into the packed triangle), warps 10..17 = converters (FUSED only).
 // Work items (job, channel, strip) are handed out dynamically (one atomic per item), channel by
 // channel, so that the strips of a channel run together and share its data in L2.
+// The default engine, FUSED_PAIR (correlate_pair_kernel, below), runs on CTA pairs with M = 256
+// pair MMAs, converters loading samples straight into registers, from an assembled frame (frame
+// mode) or from the packets through their index (packet mode, xe_correlate_packets). The legacy
+// mma.sync baseline engine is in xe_legacy.cu.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
