@@ -10,8 +10,8 @@
 //   3. copy   packet k copies its payload iff owner == k (else it is a duplicate); every slot that
 //             no packet owns is zero-filled and its 8 channels' lost counters grow by 4 samples.
 // The zero-copy path (xe_correlate_packets) runs 1 and 2 and a tally (the counts of 3 without
-// moving any payload): the owner table is then the frame's index, through which the correlator
-// reads the packets in place.
+// moving any payload, from the owner table alone): the owner table is then the frame's index,
+// through which the correlator reads the packets in place.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,48 +54,48 @@ __global__ void init_kernel(uint32_t *owner, int64_t n) {
         owner[i] = kNone;
 }
 
-__global__ void claim_kernel(const uint8_t *__restrict__ pkts, Geo g, uint32_t *owner, uint32_t *stats) {
+// count_in_window (the zero-copy path): stats[1] also grows by every in-window packet; the tally
+// then moves the owners among them from stats[1] to stats[0], leaving the duplicates in stats[1].
+__global__ void claim_kernel(const uint8_t *__restrict__ pkts, Geo g, uint32_t *owner, uint32_t *stats,
+                             int count_in_window) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     int cls = -1, slot = 0, grp = 0;
     if (k < g.n_pkts) {
         cls = classify(pkts, g, k, slot, grp);
         if (cls == kOk) atomicMin(&owner[oidx(g, slot, grp)], k);
     }
+    const uint32_t in_win = __reduce_add_sync(0xffffffffu, cls == kOk);
     const uint32_t late = __reduce_add_sync(0xffffffffu, cls == kLate);
     const uint32_t early = __reduce_add_sync(0xffffffffu, cls == kEarly);
     const uint32_t inval = __reduce_add_sync(0xffffffffu, cls == kInvalid);
     if ((threadIdx.x & 31) == 0) {
+        if (count_in_window && in_win) atomicAdd(&stats[1], in_win);
         if (late) atomicAdd(&stats[2], late);
         if (early) atomicAdd(&stats[3], early);
         if (inval) atomicAdd(&stats[4], inval);
     }
 }
 
-// Tally only (the zero-copy path): one thread per packet (threads [0, n_pkts)) and one per
-// (slot, group) after them; the ok / duplicate counts are summed per warp before their atomics.
-__global__ void tally_kernel(const uint8_t *__restrict__ pkts, Geo g, const uint32_t *__restrict__ owner,
-                             uint8_t *__restrict__ filled, uint32_t *lost, uint32_t *stats) {
-    const uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    bool ok = false, dup = false;
-    if (k < g.n_pkts) {
-        int slot = 0, grp = 0;
-        if (classify(pkts, g, (uint32_t)k, slot, grp) == kOk) {
-            ok = owner[oidx(g, slot, grp)] == (uint32_t)k;
-            dup = !ok;
-        }
-    } else if (k - g.n_pkts < (uint64_t)g.Q * g.G) {
-        const uint64_t sg = k - g.n_pkts;
+// Tally only (the zero-copy path), one thread per (slot, group): filled, lost, and the ok count.
+// Every filled slot has exactly one owner, an in-window packet, so ok = filled slots and the
+// duplicates are the in-window packets the claim counted into stats[1] less the owners: no packet
+// header is read again.
+__global__ void tally_kernel(Geo g, const uint32_t *__restrict__ owner, uint8_t *__restrict__ filled, uint32_t *lost,
+                             uint32_t *stats) {
+    const uint64_t sg = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    bool have = false;
+    if (sg < (uint64_t)g.Q * g.G) {
         const int grp = (int)(sg % g.G);
-        const bool have = owner[oidx(g, (int)(sg / g.G), grp)] != kNone;
+        have = owner[oidx(g, (int)(sg / g.G), grp)] != kNone;
         filled[sg] = have ? 1 : 0;
         if (!have) {
             for (int c = 0; c < 8; ++c) atomicAdd(&lost[8 * grp + c], 4u);
         }
     }
-    const uint32_t n_ok = __reduce_add_sync(0xffffffffu, ok), n_dup = __reduce_add_sync(0xffffffffu, dup);
-    if ((threadIdx.x & 31) == 0) {
-        if (n_ok) atomicAdd(&stats[0], n_ok);
-        if (n_dup) atomicAdd(&stats[1], n_dup);
+    const uint32_t n_ok = __reduce_add_sync(0xffffffffu, have);
+    if ((threadIdx.x & 31) == 0 && n_ok) {
+        atomicAdd(&stats[0], n_ok);
+        atomicSub(&stats[1], n_ok);
     }
 }
 
@@ -241,7 +241,7 @@ int xe_flag_counts(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, ui
     asmb::init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
     XE_TRY_CUDA(cudaGetLastError());
     if (n_pkts) {
-        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, scratch);
+        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, scratch, 0);
         XE_TRY_CUDA(cudaGetLastError());
         const uint64_t blocks = ((uint64_t)n_pkts * 32 + asmb::kFlagThreads - 1) / asmb::kFlagThreads;
         if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
@@ -288,14 +288,13 @@ static int launch(const uint8_t *pkts, const Geo &g, uint32_t *owner, uint8_t *f
     init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
     XE_TRY_CUDA(cudaGetLastError());
     if (g.n_pkts) {
-        claim_kernel<<<(g.n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats);
+        claim_kernel<<<(g.n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats, kCopy ? 0 : 1);
         XE_TRY_CUDA(cudaGetLastError());
     }
     if (!kCopy) {
-        const uint64_t threads = (uint64_t)g.n_pkts + (uint64_t)slots;
-        const uint64_t blocks = (threads + 255) / 256;
+        const uint64_t blocks = ((uint64_t)slots + 255) / 256;
         if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
-        tally_kernel<<<(unsigned)blocks, 256, 0, st>>>(pkts, g, owner, filled, lost, stats);
+        tally_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, owner, filled, lost, stats);
         XE_TRY_CUDA(cudaGetLastError());
         return XE_OK;
     }
@@ -397,7 +396,7 @@ extern "C" int xe_assemble_noalloc(const uint8_t *pkts, uint32_t n_pkts, uint32_
     asmb::init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
     XE_TRY_CUDA(cudaGetLastError());
     if (n_pkts) {
-        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats);
+        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats, 0);
         XE_TRY_CUDA(cudaGetLastError());
     }
     const uint64_t blocks = ((uint64_t)n_pkts + (uint64_t)slots + 3) / 4;
