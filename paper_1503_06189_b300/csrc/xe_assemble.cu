@@ -49,9 +49,28 @@ __device__ __forceinline__ int classify(const uint8_t *pkts, const Geo &g, uint3
     return kOk;
 }
 
+constexpr int kIndexThreads = 512;           // claim / tally block size (one counter atomic per block)
+
 __global__ void init_kernel(uint32_t *owner, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         owner[i] = kNone;
+}
+
+// Adds this block's counts v[0..n) (one value per thread, summed per warp, then per block in shared
+// memory) to dst[0..n): one global atomic per counter and block, as the counters are single words
+// every block adds to. All threads of the block must call it.
+template <int n>
+__device__ __forceinline__ void block_add(const uint32_t (&v)[n], uint32_t *const (&dst)[n]) {
+    __shared__ uint32_t part[n];
+    if (threadIdx.x < n) part[threadIdx.x] = 0;
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < n; ++c) {
+        const uint32_t w = __reduce_add_sync(0xffffffffu, v[c]);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&part[c], w);
+    }
+    __syncthreads();
+    if (threadIdx.x < n && part[threadIdx.x] && dst[threadIdx.x]) atomicAdd(dst[threadIdx.x], part[threadIdx.x]);
 }
 
 // count_in_window (the zero-copy path): stats[1] also grows by every in-window packet; the tally
@@ -64,16 +83,10 @@ __global__ void claim_kernel(const uint8_t *__restrict__ pkts, Geo g, uint32_t *
         cls = classify(pkts, g, k, slot, grp);
         if (cls == kOk) atomicMin(&owner[oidx(g, slot, grp)], k);
     }
-    const uint32_t in_win = __reduce_add_sync(0xffffffffu, cls == kOk);
-    const uint32_t late = __reduce_add_sync(0xffffffffu, cls == kLate);
-    const uint32_t early = __reduce_add_sync(0xffffffffu, cls == kEarly);
-    const uint32_t inval = __reduce_add_sync(0xffffffffu, cls == kInvalid);
-    if ((threadIdx.x & 31) == 0) {
-        if (count_in_window && in_win) atomicAdd(&stats[1], in_win);
-        if (late) atomicAdd(&stats[2], late);
-        if (early) atomicAdd(&stats[3], early);
-        if (inval) atomicAdd(&stats[4], inval);
-    }
+    const uint32_t v[4] = {cls == kOk ? 1u : 0u, cls == kLate ? 1u : 0u, cls == kEarly ? 1u : 0u,
+                           cls == kInvalid ? 1u : 0u};
+    uint32_t *const dst[4] = {count_in_window ? &stats[1] : nullptr, &stats[2], &stats[3], &stats[4]};
+    block_add(v, dst);
 }
 
 // Tally only (the zero-copy path), one thread per (slot, group): filled, lost, and the ok count.
@@ -92,11 +105,10 @@ __global__ void tally_kernel(Geo g, const uint32_t *__restrict__ owner, uint8_t 
             for (int c = 0; c < 8; ++c) atomicAdd(&lost[8 * grp + c], 4u);
         }
     }
-    const uint32_t n_ok = __reduce_add_sync(0xffffffffu, have);
-    if ((threadIdx.x & 31) == 0 && n_ok) {
-        atomicAdd(&stats[0], n_ok);
-        atomicSub(&stats[1], n_ok);
-    }
+    // ok += n, dup -= n (modulo 2^32: adding the two's complement subtracts)
+    const uint32_t v[2] = {have ? 1u : 0u, have ? 0xFFFFFFFFu : 0u};
+    uint32_t *const dst[2] = {&stats[0], &stats[1]};
+    block_add(v, dst);
 }
 
 // F-engine flags (Sec. II-C): one warp per packet; a packet that owns its slot adds the flags of its
@@ -288,13 +300,14 @@ static int launch(const uint8_t *pkts, const Geo &g, uint32_t *owner, uint8_t *f
     init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
     XE_TRY_CUDA(cudaGetLastError());
     if (g.n_pkts) {
-        claim_kernel<<<(g.n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats, kCopy ? 0 : 1);
+        claim_kernel<<<(g.n_pkts + kIndexThreads - 1) / kIndexThreads, kIndexThreads, 0, st>>>(pkts, g, owner, stats,
+                                                                                              kCopy ? 0 : 1);
         XE_TRY_CUDA(cudaGetLastError());
     }
     if (!kCopy) {
-        const uint64_t blocks = ((uint64_t)slots + 255) / 256;
+        const uint64_t blocks = ((uint64_t)slots + kIndexThreads - 1) / kIndexThreads;
         if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
-        tally_kernel<<<(unsigned)blocks, 256, 0, st>>>(g, owner, filled, lost, stats);
+        tally_kernel<<<(unsigned)blocks, kIndexThreads, 0, st>>>(g, owner, filled, lost, stats);
         XE_TRY_CUDA(cudaGetLastError());
         return XE_OK;
     }
