@@ -465,8 +465,9 @@ def run_xe(args):
 
 
 def run_engine_baselines(xe, torch, dev, reps: int = 3):
-    """The legacy warp-level engine (mma.sync m16n8k64 s4 on the packed samples) and the default
-    CTA-pair tcgen05 engine on the same assembled full-band frame (N=256, F=1024, T=4096, random
+    """The legacy warp-level engines (mma.sync m16n8k64 s4 on the packed samples, m16n8k32 s8 on
+    samples unpacked in shared memory) and the default CTA-pair tcgen05 engine on the same assembled
+    full-band frame (N=256, F=1024, T=4096, random
     bytes), best of `reps` launches each: context for what the tensor-core path buys."""
     N, F, T = N_INPUTS, N_CHAN, N_TIME
     g = torch.Generator(device=dev)
@@ -474,7 +475,8 @@ def run_engine_baselines(xe, torch, dev, reps: int = 3):
     frame = torch.randint(0, 256, (T, F, N), generator=g, device=dev, dtype=torch.int32).to(torch.uint8)
     vis = torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev)
     out = {}
-    for name, eng in (("legacy_mma_sync_s4", xe.XE_ENGINE_LEGACY_S4), ("tcgen05_pair", xe.XE_ENGINE_FUSED_PAIR)):
+    for name, eng in (("legacy_mma_sync_s4", xe.XE_ENGINE_LEGACY_S4), ("legacy_mma_sync_s8", xe.XE_ENGINE_LEGACY_S8),
+                      ("tcgen05_pair", xe.XE_ENGINE_FUSED_PAIR)):
         tune = dict(engine=eng, max_strip=0, k_flush=0, n_ctas=0)
         jobs = [(frame, vis, xe.Shape(N, F, T), False)]
         ws = torch.empty(max(1, xe.xe_correlate_batched_workspace_size(jobs, tune)), dtype=torch.uint8, device=dev)

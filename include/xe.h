@@ -143,6 +143,8 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
                                    operands straight on the packed samples (three MMAs per tile:
                                    Re V = A B^T, Im V = 2 A' B'^T - A B'^T with B' nibble-swapped and
                                    A' the Im nibbles); max_strip, k_flush and n_ctas are ignored */
+#define XE_ENGINE_LEGACY_S8 6   /* baseline, no tcgen05: as LEGACY_S4 with mma.sync m16n8k32 on int8 (re, im)
+                                   pairs unpacked in shared memory */
 
 typedef struct {
     int32_t engine;      /* XE_ENGINE_* */

@@ -20,7 +20,7 @@ XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ENOMEM, XE_ECUDA, XE_ETIMEOUT, XE_EAGAIN = 0,
 XE_MAX_TIME = (1 << 24) - 1
 XE_MAX_JOBS = 64
 XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K, XE_ENGINE_FUSED_PAIR = 0, 1, 2, 3, 4
-XE_ENGINE_LEGACY_S4 = 5
+XE_ENGINE_LEGACY_S4, XE_ENGINE_LEGACY_S8 = 5, 6
 
 EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",

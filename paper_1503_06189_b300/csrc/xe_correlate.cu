@@ -55,7 +55,7 @@ constexpr int kDefaultKFlush = 1 << 15;
 constexpr int kMaxKFlush = 1 << 15;
 constexpr int kConvWarps = 8;
 
-enum Engine { kUnpackedK = 0, kUnpackedMN = 1, kFusedMN = 2, kFusedPair = 3, kLegacyS4 = 4 };
+enum Engine { kUnpackedK = 0, kUnpackedMN = 1, kFusedMN = 2, kFusedPair = 3, kLegacyS4 = 4, kLegacyS8 = 5 };
 
 struct Job {                 // 128-byte aligned through its CUtensorMap
     CUtensorMap tmap;        // operand map (unpacked engines) or packed frame map (fused)
@@ -1323,7 +1323,7 @@ static JobGeom geom(const xe_shape &s, int engine) {
     g.nb = g.R / kBlk;
     g.ldy = round_up(std::max<int64_t>(s.n_time, 1), kKtMax);
     g.k_tiles = (int)((s.n_time + kt - 1) / kt);
-    g.y_bytes = (engine == kFusedMN || engine == kFusedPair || engine == kLegacyS4)
+    g.y_bytes = (engine == kFusedMN || engine == kFusedPair || engine == kLegacyS4 || engine == kLegacyS8)
                     ? 0 : (size_t)round_up((int64_t)s.n_chan * g.R * g.ldy, 1024);
     return g;
 }
@@ -1342,6 +1342,7 @@ static int engine_of(int api_engine) {
         case XE_ENGINE_UNPACKED_K: return kUnpackedK;
         case XE_ENGINE_FUSED_PAIR: return kFusedPair;
         case XE_ENGINE_LEGACY_S4: return kLegacyS4;
+        case XE_ENGINE_LEGACY_S8: return kLegacyS8;
         default: return -1;
     }
 }
@@ -1462,9 +1463,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         if (int e = check_job(jobs[j].s, src, jobs[j].vis)) return e;
         if (pk && (!pk[j].owner || pk[j].pkt_stride % 16 || s_chan_misfit(jobs[j].s))) return XE_EINVAL;
     }
-    if (engine == kLegacyS4) {                  // the baseline path: no workspace, no tcgen05
+    if (engine == kLegacyS4 || engine == kLegacyS8) {   // the baseline paths: no workspace, no tcgen05
         if (!ws || ws_bytes < batched_ws(jobs, n_jobs, engine)) return XE_ENOMEM;
-        return legacy::correlate_s4(jobs, n_jobs, st);
+        return legacy::correlate_legacy(jobs, n_jobs, engine == kLegacyS8, st);
     }
     if (!ws || ws_bytes < batched_ws(jobs, n_jobs, engine)) return XE_ENOMEM;
     if (reinterpret_cast<uintptr_t>(ws) & 15) return XE_EINVAL;

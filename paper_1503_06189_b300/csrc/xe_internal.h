@@ -65,8 +65,9 @@ int correlate_packets_batched(const xe_job *jobs, const packet_src *src, int n_j
                               cudaStream_t st);
 
 namespace legacy {
-// XE_ENGINE_LEGACY_S4: the jobs (checked by the caller) on the mma.sync 4-bit path, one launch per job.
-int correlate_s4(const xe_job *jobs, int n_jobs, cudaStream_t st);
+// XE_ENGINE_LEGACY_S4 / _S8: the jobs (checked by the caller) on the mma.sync 4-bit path or its int8
+// variant (s8), one launch per job.
+int correlate_legacy(const xe_job *jobs, int n_jobs, bool s8, cudaStream_t st);
 }  // namespace legacy
 
 inline bool valid_shape(const xe_shape &s) {

@@ -1,6 +1,6 @@
 // xe_legacy.cu -- A3/A4 on the legacy warp-level tensor path: mma.sync m16n8k64 with 4-bit signed
-// operands, straight on the packed samples (no unpack, no tcgen05). A baseline for the tcgen05
-// engines, measured beside them.
+// operands, straight on the packed samples (no unpack, no tcgen05), and its m16n8k32 s8 variant on
+// samples unpacked in shared memory. Baselines for the tcgen05 engines, measured beside them.
 //
 // Method (Sec. I, Sec. II-B): V_f[i,j] = sum_t x_i(t) conj(x_j(t)), i <= j, x = re + i im. A sample
 // byte is re << 4 | im, so four consecutive samples of one input, as one 32-bit register, are the
@@ -135,7 +135,120 @@ __global__ void __launch_bounds__(kThreads) correlate_s4_kernel(const uint8_t *_
     }
 }
 
-int correlate_s4(const xe_job *jobs, int n_jobs, cudaStream_t st) {
+// ------------------------------------------------------------------ s8 variant (XE_ENGINE_LEGACY_S8)
+// The same method on int8 operands, m16n8k32 (16 samples per MMA): the loader unpacks every sample
+// once, into shared rows of (re, im) int8 pairs [64 inputs][2 x 128 samples]; B' swaps the bytes of
+// each pair (im, re) and A' clears the re bytes (0, im). Three MMAs per 16 x 8 tile and 16 samples.
+constexpr int kRowWords8 = 68;     // 64 words of (re, im) pairs + 4 of padding
+
+__device__ __forceinline__ void mma_s8(int (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k32.row.col.s32.s8.s8.s32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+r"(d[0]), "+r"(d[1]), "+r"(d[2]), "+r"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Two packed samples (the low 16 bits of h: bytes re << 4 | im) -> int8 bytes (re0, im0, re1, im1).
+// Each byte's nibble v in [0, 15] becomes v - 16 [v >= 8]: OR in 0xF0 where bit 3 is set; (v & 8) x 30
+// = 240 stays inside its byte, so one multiply fills all four.
+__device__ __forceinline__ uint32_t unpack2_s8(uint32_t h) {
+    const uint32_t x = __byte_perm(h, 0, 0x1100);                     // (p0, p0, p1, p1)
+    const uint32_t v = ((x >> 4) & 0x000F000Fu) | (x & 0x0F000F00u);   // (re0, im0, re1, im1) as nibbles
+    return v | ((v & 0x08080808u) * 0x1Eu);
+}
+
+__global__ void __launch_bounds__(kThreads) correlate_s8_kernel(const uint8_t *__restrict__ frame, int N, int F,
+                                                                int T, int32_t *__restrict__ vis, int accumulate) {
+    __shared__ uint32_t sa[kTile * kRowWords8];
+    __shared__ uint32_t sb[kTile * kRowWords8];
+    const int nbk = (N + kTile - 1) / kTile;
+    int q = blockIdx.x, I = 0;
+    while (q >= nbk - I) {
+        q -= nbk - I;
+        ++I;
+    }
+    const int J = I + q;
+    const bool diag = I == J;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wi = warp & 3, wj = warp >> 2;
+    const int g = lane >> 2, tq = lane & 3;
+    const int tb = threadIdx.x & 31, ng = threadIdx.x >> 5;
+    const int64_t P = (int64_t)N * (N + 1) / 2;
+
+    for (int f = blockIdx.y; f < F; f += gridDim.y) {
+        int acc_re[4][4] = {}, acc_s[4][4] = {}, acc_x[4][4] = {};
+        for (int t0 = 0; t0 < T; t0 += kKt) {
+            __syncthreads();
+            for (int which = 0; which < (diag ? 1 : 2); ++which) {
+                const int n0 = (which ? J : I) * kTile + ng * 8;
+                uint32_t w[4][2];
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    const int t = t0 + tb * 4 + s;
+                    uint2 v = make_uint2(0u, 0u);
+                    if (t < T && n0 < N) v = *reinterpret_cast<const uint2 *>(frame + ((size_t)t * F + f) * N + n0);
+                    w[s][0] = v.x;
+                    w[s][1] = v.y;
+                }
+                uint32_t *dst = which ? sb : sa;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {     // input n0 + k, samples 4 tb .. 4 tb + 3 -> words 2 tb, 2 tb + 1
+                    const int h = k >> 2, b = k & 3;
+                    const uint32_t sel = (uint32_t)(b | ((b + 4) << 4));
+                    const uint32_t lo = __byte_perm(w[0][h], w[1][h], sel);     // samples 0, 1 in bytes 0, 1
+                    const uint32_t hi = __byte_perm(w[2][h], w[3][h], sel);     // samples 2, 3
+                    uint2 o = make_uint2(unpack2_s8(lo), unpack2_s8(hi));
+                    *reinterpret_cast<uint2 *>(&dst[(ng * 8 + k) * kRowWords8 + 2 * tb]) = o;
+                }
+            }
+            __syncthreads();
+            const uint32_t *sB = diag ? sa : sb;
+#pragma unroll
+            for (int kk = 0; kk < kKt / 16; ++kk) {   // 16 samples = 32 int8 = 8 words per step
+                const int kw = kk * 8;
+                const uint32_t *ra = sa + (wi * 16 + g) * kRowWords8 + kw + tq;
+                uint32_t a[4], am[4];
+                a[0] = ra[0];
+                a[1] = ra[8 * kRowWords8];
+                a[2] = ra[4];
+                a[3] = ra[8 * kRowWords8 + 4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) am[r] = a[r] & 0xFF00FF00u;   // (0, im) pairs
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt) {
+                    const uint32_t *rb = sB + (wj * 32 + nt * 8 + g) * kRowWords8 + kw + tq;
+                    const uint32_t b0 = rb[0], b1 = rb[4];
+                    const uint32_t s0 = __byte_perm(b0, 0, 0x2301), s1 = __byte_perm(b1, 0, 0x2301);   // (im, re)
+                    mma_s8(acc_re[nt], a, b0, b1);
+                    mma_s8(acc_s[nt], a, s0, s1);
+                    mma_s8(acc_x[nt], am, s0, s1);
+                }
+            }
+        }
+        int32_t *vis_f = vis + (size_t)f * (size_t)P * 2;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = I * kTile + wi * 16 + g + (r >> 1) * 8;
+                const int j = J * kTile + wj * 32 + nt * 8 + 2 * tq + (r & 1);
+                if (i >= N || j >= N || j < i) continue;
+                const int64_t p = (int64_t)i * N - (int64_t)i * (i - 1) / 2 + (j - i);
+                const int re = acc_re[nt][r];
+                const int im = (int)(2u * (uint32_t)acc_x[nt][r] - (uint32_t)acc_s[nt][r]);
+                int2 *o = reinterpret_cast<int2 *>(vis_f) + p;
+                if (accumulate) {
+                    const int2 v = *o;
+                    *o = make_int2((int)((uint32_t)v.x + (uint32_t)re), (int)((uint32_t)v.y + (uint32_t)im));
+                } else {
+                    *o = make_int2(re, im);
+                }
+            }
+        }
+    }
+}
+
+int correlate_legacy(const xe_job *jobs, int n_jobs, bool s8, cudaStream_t st) {
     for (int j = 0; j < n_jobs; ++j) {
         const xe_shape &s = jobs[j].s;
         if (s.n_time == 0) {                      // empty integration: V = 0, or unchanged when adding
@@ -147,8 +260,13 @@ int correlate_s4(const xe_job *jobs, int n_jobs, cudaStream_t st) {
         }
         const int nbk = (s.n_inputs + kTile - 1) / kTile;
         dim3 grid((unsigned)(nbk * (nbk + 1) / 2), (unsigned)(s.n_chan < 65535 ? s.n_chan : 65535), 1);
-        correlate_s4_kernel<<<grid, kThreads, 0, st>>>(static_cast<const uint8_t *>(jobs[j].frame), s.n_inputs,
-                                                       s.n_chan, s.n_time, jobs[j].vis, jobs[j].accumulate ? 1 : 0);
+        const uint8_t *fr = static_cast<const uint8_t *>(jobs[j].frame);
+        if (s8)
+            correlate_s8_kernel<<<grid, kThreads, 0, st>>>(fr, s.n_inputs, s.n_chan, s.n_time, jobs[j].vis,
+                                                           jobs[j].accumulate ? 1 : 0);
+        else
+            correlate_s4_kernel<<<grid, kThreads, 0, st>>>(fr, s.n_inputs, s.n_chan, s.n_time, jobs[j].vis,
+                                                           jobs[j].accumulate ? 1 : 0);
         if (cudaError_t e = cudaGetLastError()) return cuda_fail(e);
     }
     return XE_OK;

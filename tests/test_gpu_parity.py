@@ -82,7 +82,7 @@ def test_correlate_worst_case_magnitudes():
     assert_vis_equal(X.correlate(fr), want)
 
 
-@pytest.mark.parametrize("engine", [xe.XE_ENGINE_FUSED_PAIR, xe.XE_ENGINE_LEGACY_S4])
+@pytest.mark.parametrize("engine", [xe.XE_ENGINE_FUSED_PAIR, xe.XE_ENGINE_LEGACY_S4, xe.XE_ENGINE_LEGACY_S8])
 def test_correlate_int32_limit_closed_form(engine):
     """Every sample -8-8i over the longest integration the int32 output holds (T = 2^24 - 1): each
     visibility is T (-8-8i)(-8+8i) = 128 T = 2,147,483,520 + 0i, 128 below 2^31 (closed form)."""
@@ -93,13 +93,14 @@ def test_correlate_int32_limit_closed_form(engine):
     assert (g[..., 0] == 128 * T).all() and (g[..., 1] == 0).all()
 
 
-def test_legacy_engine_accumulates():
-    """The legacy mma.sync engine adds to the visibilities of an earlier call (Sec. II-B)."""
+@pytest.mark.parametrize("engine", [xe.XE_ENGINE_LEGACY_S4, xe.XE_ENGINE_LEGACY_S8])
+def test_legacy_engine_accumulates(engine):
+    """The legacy mma.sync engines add to the visibilities of an earlier call (Sec. II-B)."""
     a = synth.signal_frame(96, 3, 700, 11)
     b = synth.signal_frame(96, 3, 260, 12)
     va, _ = oracle.correlate(a)
     vb, _ = oracle.correlate(b)
-    tune = dict(engine=xe.XE_ENGINE_LEGACY_S4, max_strip=0, k_flush=0, n_ctas=0)
+    tune = dict(engine=engine, max_strip=0, k_flush=0, n_ctas=0)
     fa, fb = X.dev(a), X.dev(b)
     s_a, s_b = xe.Shape(96, 3, 700), xe.Shape(96, 3, 260)
     vis = torch.full((3, xe.npairs(96), 2), -5, dtype=torch.int32, device="cuda")
@@ -137,7 +138,7 @@ def test_correlate_workspace_too_small():
 
 
 ENGINES = [xe.XE_ENGINE_FUSED, xe.XE_ENGINE_UNPACKED, xe.XE_ENGINE_UNPACKED_K, xe.XE_ENGINE_FUSED_PAIR,
-           xe.XE_ENGINE_LEGACY_S4]
+           xe.XE_ENGINE_LEGACY_S4, xe.XE_ENGINE_LEGACY_S8]
 
 
 @pytest.mark.parametrize("engine", ENGINES)
