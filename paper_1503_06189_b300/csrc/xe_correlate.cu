@@ -639,7 +639,8 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
 // warp on different roles run their branches in turn, and a lane suspended in an mbarrier wait
 // would hold up the lane it waits for.
 
-constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA: A, B
+constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA: A, B (a twin: A of channels
+                                              // f and f + 1; a wide stage: A, samples kKt further on)
 constexpr int kPairEpiWarps = 4;              // one per TMEM lane quarter (accumulator double-buffered)
 constexpr int kPairConvFwdWarp = 2;           // forwards converter completion, prefetches into L2
 constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
@@ -794,8 +795,9 @@ struct PairCursor {
 constexpr uint32_t kNoPacket = 0xFFFFFFFFu;
 
 // One converter thread's walk over the stages of its pair. The thread converts inputs 16c ..
-// 16c + 15 of the A block and (off the diagonal) of the B block, for samples t_row + r kRowStep
-// (r < kRows) of each kKt-sample stage; a stage's address arithmetic is two 64-bit adds.
+// 16c + 15 of the A block and (unless the item is a plain diagonal single) of the B slot's block,
+// for samples t_row + r kRowStep (r < kRows) of each kKt-sample stage; a stage's address
+// arithmetic is two 64-bit adds.
 // Frame mode: sample t of these bytes sits at frame + (t F + f) N + column.
 // Packet mode (the zero-copy path): sample t sits in packet o = owner[f / 8][t / 4] (the packet
 // holding time slot t / 4 of this channel's group), at pkts + o * pkt_stride + 16 + ((t % 4) 8 +
