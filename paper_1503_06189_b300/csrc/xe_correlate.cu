@@ -929,7 +929,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < p.op_stages; ++s) {
-            dev::mbar_init(&op_full[s], 2);         // one arrival per CTA of the pair
+            // one arrival per CTA of the pair (frame mode: the forwarders), or per converter warp
+            dev::mbar_init(&op_full[s], kPackets ? 2 * kPairConvWarps : 2);
             dev::mbar_init(&op_empty[s], 1);
             dev::mbar_init(&conv_done[s], kPairConvWarps);
         }
@@ -971,13 +972,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
     };
 
     if (warp == kPairConvFwdWarp) {
-        if (lane == 0) {
+        if (!kPackets && lane == 0) {
             // ---------------------------------------------------------------- converter forwarder
-            // once all converter warps of this CTA finished a stage: tell the even CTA's MMA thread
-            // (one arrival per CTA and stage), then prefetch a later stage's packed tiles into L2
-            // (frame mode: packets have no tensor map)
+            // frame mode: once all converter warps of this CTA finished a stage, tell the even CTA's
+            // MMA thread (one arrival per CTA and stage), then prefetch a later stage's packed tiles
+            // into L2. Packet mode has no tensor map to prefetch with: its converter warps arrive on
+            // the even CTA's barrier themselves (the forwarder's hop measured 2-4 % of a call)
             auto prefetch = [&](const PairCursor &c) {
-                if (kPackets) return;
                 const CUtensorMap *map = &p.jobs[c.job].tmap;
                 dev::tma_prefetch_l2_3d(map, (2 * c.R + (int)rank) * 64, c.f, c.kt * kKt);
                 if (c.R != c.C) dev::tma_prefetch_l2_3d(map, (2 * c.C + (int)rank) * 64, c.f, c.kt * kKt);
@@ -1262,7 +1263,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             }
             dev::fence_proxy_async_smem();            // operand visible to the tensor core
             __syncwarp();
-            if (lane == 0) dev::mbar_arrive(&conv_done[os]);
+            if (lane == 0) {
+                if constexpr (kPackets) dev::mbar_arrive_remote(&op_full[os], 0);
+                else dev::mbar_arrive(&conv_done[os]);
+            }
             if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
             return true;
         };
