@@ -491,10 +491,56 @@ def run_engine_baselines(xe, torch, dev, reps: int = 3):
             best = ms if best is None else min(best, ms)
         out[name] = {"ms_per_frame": best, "value": cmac_per_frame() / (best / 1e3), "unit": "CMAC/s"}
         del ws
+    out["per_channel_launches"] = run_per_channel_launches(xe, torch, dev, frame, vis, reps)
     del frame, vis
     torch.cuda.empty_cache()
     out["workload"] = "one assembled full-band frame, N=256, F=1024, T=4096, random bytes, xe_correlate_batched"
     return out
+
+
+def run_per_channel_launches(xe, torch, dev, frame, vis, reps: int = 3):
+    """The plain form of the same correlation: one xe_correlate launch per channel (F = 1), each on
+    that channel's samples copied to a contiguous [T][1][N] frame before timing, issued one after
+    the other on one stream; also replayed from a CUDA graph holding those launches (no host launch
+    cost). `vis` holds the batched launch's result (the last engine run above, on the same frame);
+    both forms must reproduce it bit for bit."""
+    N, F, T = N_INPUTS, N_CHAN, N_TIME
+    s1 = xe.Shape(N, 1, T)
+    per = frame.permute(1, 0, 2).contiguous()               # [F][T][N] = F frames of [T][1][N]
+    got = torch.full_like(vis, -1)
+    ws = torch.empty(max(1, xe.xe_correlate_workspace_size(s1)), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    def launches():
+        for f in range(F):
+            xe.xe_correlate(per[f], s1, got[f], False, ws, stream=stream)
+
+    def timed(fn):
+        best = None
+        for _ in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return best
+
+    with torch.cuda.stream(stream):
+        plain_ms = timed(launches)
+        identical = bool(torch.equal(got, vis))
+        got.fill_(-1)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            launches()
+        graph_ms = timed(graph.replay)
+        identical = identical and bool(torch.equal(got, vis))
+    del graph, per, got, ws
+    torch.cuda.empty_cache()
+    return {"launches": F, "ms_per_frame": plain_ms, "value": cmac_per_frame() / (plain_ms / 1e3),
+            "graph_ms_per_frame": graph_ms, "graph_value": cmac_per_frame() / (graph_ms / 1e3),
+            "unit": "CMAC/s", "identical_to_batched": identical}
 
 
 def load_traffic():

@@ -210,6 +210,25 @@ def test_correlate_deterministic():
     assert torch.equal(a, b)
 
 
+def test_batched_launch_equals_plain_per_channel_launches():
+    """All channels of a frame in one launch give exactly what one plain launch per channel gives
+    (each channel's samples copied to a contiguous [T][1][N] frame first), and both match the
+    oracle. N = 256 makes three 256x256 blocks per channel; T is ragged."""
+    N, F, T = 256, 6, 1000
+    fr = synth.signal_frame(N, F, T, 91)
+    want, _ = oracle.correlate(fr)
+    batched = X.correlate(fr)
+    frame = X.dev(fr)
+    s1 = xe.Shape(N, 1, T)
+    ws = torch.empty(max(1, xe.xe_correlate_workspace_size(s1)), dtype=torch.uint8, device="cuda")
+    per = torch.full_like(batched, 0x7EADBEEF)
+    for f in range(F):
+        xe.xe_correlate(frame[:, f:f + 1, :].contiguous(), s1, per[f], False, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(per, batched)
+    assert_vis_equal(per, want)
+
+
 def test_correlate_pathfinder_frame_sampled():
     """Per-server Pathfinder frame: N=256, F=64, T=16384 (256 MiB), signal model. The oracle checks 6
     channels spread over the frame; all channels are compared against a second launch with a
