@@ -149,3 +149,50 @@ def test_packets_full_band_frame_matches_two_step_path_and_oracle_sample():
         want, st = oracle.correlate(frame_o, f, 1)
         assert st == oracle.OK
         np.testing.assert_array_equal(_host(vis[f:f + 1], np.int64), want)
+
+
+def test_packets_bench_launch_eight_frames_accumulating():
+    """The bench's main launch at full size: the full band (N=256, F=1024, 128 streams of one
+    8-channel group each) over 8 consecutive frames of T=4096 in one call (T=32768, so channel pairs
+    take the twin layout), 0.1% of packets dropped, adding onto visibilities that already hold an
+    earlier integration. Every channel is compared with xe_assemble followed by xe_correlate on the
+    device (accumulating onto the same start values); the oracle checks two 8-channel groups, each
+    assembled on the host from that group's packets alone (placement is per group, so the subset
+    assembles to the same group frame)."""
+    N, F, T, gps = 256, 1024, 8 * 4096, 1
+    s = xe.Shape(N, F, T)
+    fr = synth.signal_frame_torch(N, F, T, 70, device="cuda")
+    pk = synth.packetize_torch(fr, 0, gps)
+    del fr
+    g = torch.Generator(device="cuda")
+    g.manual_seed(71)
+    keep = torch.rand(pk.shape[0], generator=g, device="cuda") >= 0.001
+    pk = pk[keep].contiguous()
+    torch.cuda.empty_cache()
+    start = torch.randint(-(1 << 20), 1 << 20, (F, xe.npairs(N), 2), generator=g, device="cuda", dtype=torch.int32)
+    vis, filled, lost, stats = _packets_gpu(pk, 0, gps, N, F, T, vis=start.clone(), accumulate=True)
+
+    frame = torch.empty((T, F, N), dtype=torch.uint8, device="cuda")
+    filled2 = torch.empty_like(filled)
+    lost2 = torch.zeros_like(lost)
+    stats2 = torch.zeros_like(stats)
+    ws = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device="cuda")
+    xe.xe_assemble(pk, pk.shape[0], pk.shape[1], 0, gps, s, frame, filled2, lost2, stats2, ws)
+    vis2 = X.correlate(frame, vis=start.clone(), accumulate=True)
+    del frame, ws
+    assert torch.equal(vis, vis2)
+    assert torch.equal(filled, filled2) and torch.equal(lost, lost2) and torch.equal(stats, stats2)
+    assert int(stats[0]) == int(keep.sum()) and int(lost.sum()) > 0
+
+    sid = pk[:, :4].contiguous().view(torch.int32)[:, 0] & 0xFFFF
+    for grp, chans in ((5, (0, 7)), (127, (3,))):
+        sub = pk[sid == grp].clone()
+        sub[:, 0:2] = 0                                     # stream id -> 0: the group alone, F = 8
+        frame_o, _, lost_o, _ = oracle.assemble(sub.cpu().numpy(), 0, gps, N, 8, T)
+        np.testing.assert_array_equal(_host(lost[8 * grp:8 * grp + 8], np.uint32), lost_o)
+        for c in chans:
+            want, st = oracle.correlate(frame_o, c, 1)
+            assert st == oracle.OK
+            f = 8 * grp + c
+            want = want + _host(start[f:f + 1], np.int64)
+            np.testing.assert_array_equal(_host(vis[f:f + 1], np.int64), want)
