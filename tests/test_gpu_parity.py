@@ -203,6 +203,37 @@ def test_correlate_batched_uneven():
         assert_vis_equal(g, want)
 
 
+def test_correlate_maximum_inputs():
+    """N = 4096, the largest input count the library accepts (8,390,656 visibilities per channel, 32
+    blocks of 256 rows), with a ragged time tail, on the default engine and on the single-CTA and
+    legacy engines."""
+    N, F, T = 4096, 1, 300
+    fr = synth.uniform_frame(N, F, T, 4096)
+    want, st = oracle.correlate(fr)
+    assert st == oracle.OK
+    assert_vis_equal(X.correlate(fr), want)
+    for engine in (xe.XE_ENGINE_FUSED, xe.XE_ENGINE_LEGACY_S8):
+        (got,) = X.correlate_batched([fr], tune=dict(engine=engine, max_strip=0, k_flush=0, n_ctas=0))
+        assert_vis_equal(got, want)
+
+
+def test_correlate_batched_maximum_jobs():
+    """XE_MAX_JOBS frames of different N, F and T in one launch, each bit-exact; one job more is
+    rejected."""
+    shapes = [(16 * (1 + k % 6), 1 + k % 3, 64 + 37 * k) for k in range(xe.XE_MAX_JOBS)]
+    frames = [synth.uniform_frame(N, F, T, 900 + k) for k, (N, F, T) in enumerate(shapes)]
+    got = X.correlate_batched(frames)
+    for fr, g in zip(frames, got):
+        want, _ = oracle.correlate(fr)
+        assert_vis_equal(g, want)
+    fr = X.dev(frames[0])
+    vis = torch.zeros((fr.shape[1], xe.npairs(fr.shape[2]), 2), dtype=torch.int32, device="cuda")
+    jobs = [(fr, vis, xe.Shape(fr.shape[2], fr.shape[1], fr.shape[0]), False)] * (xe.XE_MAX_JOBS + 1)
+    with pytest.raises(xe.XeError) as e:
+        xe.xe_correlate_batched(jobs, torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
+    assert e.value.status == xe.XE_EINVAL
+
+
 def test_correlate_deterministic():
     fr = synth.uniform_frame(256, 2, 1024, 77)
     a = X.correlate(fr).cpu()
