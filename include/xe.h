@@ -177,7 +177,8 @@ int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate,
  * Rate probe of the legacy warp-level integer tensor path (the baseline XE_ENGINE_LEGACY_S4 runs
  * on): `blocks` CTAs of 256 threads, each warp issuing iters x 8 independent mma.sync with
  * register operands. kind 0: m16n8k64 s4 x s4 -> s32 (16,384 int ops per instruction); kind 1:
- * m16n8k32 s8 x s8 -> s32 (8,192). The caller times the launch on `stream`.
+ * m16n8k32 s8 x s8 -> s32 (8,192); kind 2: the CUDA-core dp4a (four int8 products added to an
+ * int32; 256 int ops per warp instruction), for comparison. The caller times the launch on `stream`.
  *   sink   device, int32 [blocks * 256]: written (keeps the results live), values meaningless.
  * Errors: XE_EINVAL (kind, blocks < 1, iters < 1, sink NULL), XE_ECUDA.
  */

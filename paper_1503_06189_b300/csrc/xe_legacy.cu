@@ -274,7 +274,8 @@ int correlate_legacy(const xe_job *jobs, int n_jobs, bool s8, cudaStream_t st) {
 
 // Rate probe: every warp issues chains of independent mma.sync on register operands (8 chains, so
 // the pipe never waits for a result); kind 0 = m16n8k64 s4 (16,384 int ops per instruction),
-// kind 1 = m16n8k32 s8 (8,192).
+// kind 1 = m16n8k32 s8 (8,192); kind 2 = the CUDA-core 4-way int8 dot product dp4a (8 int ops per
+// thread and instruction, 256 per warp instruction), in 8 independent chains per thread.
 __global__ void __launch_bounds__(kThreads) mma_probe_kernel(int kind, int iters, int32_t *sink) {
     uint32_t a[4] = {threadIdx.x * 0x01010101u, threadIdx.x ^ 0x5A5A5A5Au, blockIdx.x * 0x11111111u, 0x12345678u};
     const uint32_t b0 = threadIdx.x * 0x9E3779B9u, b1 = blockIdx.x ^ 0xA5A5A5A5u;
@@ -283,6 +284,12 @@ __global__ void __launch_bounds__(kThreads) mma_probe_kernel(int kind, int iters
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
             for (int k = 0; k < 8; ++k) mma_s4(acc[k], a, b0 + k, b1);
+        }
+    } else if (kind == 2) {
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                asm volatile("dp4a.s32.s32 %0, %1, %2, %0;" : "+r"(acc[k][0]) : "r"(a[k & 3]), "r"(b0 + k));
         }
     } else {
         for (int i = 0; i < iters; ++i) {
@@ -304,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) mma_probe_kernel(int kind, int iters
 }  // namespace xe
 
 extern "C" int xe_probe_mma_legacy(int32_t kind, int32_t blocks, int32_t iters, int32_t *sink, void *stream) {
-    if ((kind != 0 && kind != 1) || blocks < 1 || iters < 1 || !sink) return XE_EINVAL;
+    if (kind < 0 || kind > 2 || blocks < 1 || iters < 1 || !sink) return XE_EINVAL;
     xe::legacy::mma_probe_kernel<<<blocks, xe::legacy::kThreads, 0, static_cast<cudaStream_t>(stream)>>>(kind, iters,
                                                                                                          sink);
     if (cudaError_t e = cudaGetLastError()) return xe::cuda_fail(e);

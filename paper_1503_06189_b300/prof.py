@@ -137,11 +137,12 @@ def main(argv=None):
         print(f"flags N={N} F={F} T={T}: best {best:.4f} ms for {pk.numel() / 1e6:.0f} MB of packets, "
               f"{float(np.mean(fl)) * 100:.3f}% of samples flagged", flush=True)
     elif a.op == "mma_legacy":
-        # rate of the legacy warp-level integer tensor path (what XE_ENGINE_LEGACY_S4 runs on)
+        # rates of the legacy warp-level integer tensor path (what the LEGACY engines run on) and of dp4a
         blocks = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
         sink = torch.empty(blocks * 256, dtype=torch.int32, device=dev)
-        for kind, name, ops in ((0, "m16n8k64 s4", 16384), (1, "m16n8k32 s8", 8192)):
-            iters = 4000
+        for kind, name, ops in ((0, "mma.sync m16n8k64 s4", 16384), (1, "mma.sync m16n8k32 s8", 8192),
+                                (2, "dp4a s8 (CUDA cores)", 256)):
+            iters = 4000 if kind < 2 else 40000
             xe.xe_probe_mma_legacy(kind, blocks, 10, sink)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -150,7 +151,7 @@ def main(argv=None):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             total = blocks * 8 * iters * 8 * ops
-            print(f"mma.sync {name}: {total / ms / 1e9:.1f} T int-op/s ({blocks} CTAs x 8 warps x {iters} x 8 "
+            print(f"{name}: {total / ms / 1e9:.1f} T int-op/s ({blocks} CTAs x 8 warps x {iters} x 8 "
                   f"instructions in {ms:.3f} ms)", flush=True)
     else:
         lost = torch.zeros(F, dtype=torch.int32, device=dev)

@@ -416,3 +416,15 @@ def test_bounded_wait_times_out_and_context_survives():
     fr = synth.uniform_frame(16, 1, 256, 3)
     want, _ = oracle.correlate(fr)
     assert_vis_equal(X.correlate(fr), want)
+
+
+def test_rate_probe_kinds():
+    """The instruction-rate probe runs its three kinds (mma.sync s4, mma.sync s8, dp4a) and rejects
+    any other."""
+    sink = torch.zeros(2 * 256, dtype=torch.int32, device="cuda")
+    for kind in (0, 1, 2):
+        xe.xe_probe_mma_legacy(kind, 2, 3, sink)
+    torch.cuda.synchronize()
+    with pytest.raises(xe.XeError) as e:
+        xe.xe_probe_mma_legacy(3, 2, 3, sink)
+    assert e.value.status == xe.XE_EINVAL
