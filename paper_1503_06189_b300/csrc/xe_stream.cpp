@@ -150,6 +150,24 @@ static uint64_t newer_packets(const xe_stream *rt, const PerStream &ps, int64_t 
     return n;
 }
 
+// Releases the device resources xe_stream_create acquired; any of them may be missing (a create
+// that failed part-way). Used on create's failure paths and by xe_stream_destroy.
+static void free_runtime(xe_stream *rt) {
+    for (cudaStream_t st : rt->cs) cudaStreamDestroy(st);
+    for (auto &ps : rt->streams) {
+        if (ps->copy) cudaStreamDestroy(ps->copy);
+        for (Region &r : ps->regions) {
+            if (r.copied) cudaEventDestroy(r.copied);
+            if (r.consumed) cudaEventDestroy(r.consumed);
+        }
+    }
+    if (rt->pool) cudaFree(rt->pool);
+    rt->cs.clear();
+    rt->ws_c.clear();
+    rt->streams.clear();
+    rt->pool = nullptr;
+}
+
 static void on_batch_done(void *p) {
     BatchRec *rec = static_cast<BatchRec *>(p);
     xe_stream *rt = rec->rt;
@@ -305,22 +323,31 @@ int xe_stream_create(const xe_stream_cfg *cfg, xe_stream **out) {
     }
     uint8_t *p = static_cast<uint8_t *>(rt->pool);
     auto take = [&](size_t b) { uint8_t *q = p; p += al(b); return q; };
-    for (int s = 0; s < c.n_streams; ++s) {
-        auto ps = std::make_unique<PerStream>();
-        ps->regions.resize(c.ring_frames);
-        for (Region &r : ps->regions) {
-            r.dev = take((size_t)rt->cap * c.pkt_stride);
-            XE_TRY_CUDA(cudaEventCreateWithFlags(&r.copied, cudaEventDisableTiming));
-            XE_TRY_CUDA(cudaEventCreateWithFlags(&r.consumed, cudaEventDisableTiming));
+    // events and streams; each is registered in rt before it is created, so that a failure part-way
+    // releases everything created so far
+    auto create_handles = [&]() -> int {
+        for (int s = 0; s < c.n_streams; ++s) {
+            rt->streams.push_back(std::make_unique<PerStream>());
+            PerStream &ps = *rt->streams.back();
+            ps.regions.resize(c.ring_frames);
+            for (Region &r : ps.regions) {
+                r.dev = take((size_t)rt->cap * c.pkt_stride);
+                XE_TRY_CUDA(cudaEventCreateWithFlags(&r.copied, cudaEventDisableTiming));
+                XE_TRY_CUDA(cudaEventCreateWithFlags(&r.consumed, cudaEventDisableTiming));
+            }
+            XE_TRY_CUDA(cudaStreamCreateWithFlags(&ps.copy, cudaStreamNonBlocking));
         }
-        XE_TRY_CUDA(cudaStreamCreateWithFlags(&ps->copy, cudaStreamNonBlocking));
-        rt->streams.push_back(std::move(ps));
-    }
-    for (int i = 0; i < c.n_cuda_streams; ++i) {
-        cudaStream_t st;
-        XE_TRY_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-        rt->cs.push_back(st);
-        rt->ws_c.push_back(take(rt->ws_c_bytes));
+        for (int i = 0; i < c.n_cuda_streams; ++i) {
+            cudaStream_t st;
+            XE_TRY_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+            rt->cs.push_back(st);
+            rt->ws_c.push_back(take(rt->ws_c_bytes));
+        }
+        return XE_OK;
+    };
+    if (int e = create_handles()) {
+        free_runtime(rt.get());
+        return e;
     }
     for (int i = 0; i < slots; ++i) {
         Slot sl;
@@ -485,13 +512,7 @@ int xe_stream_destroy(xe_stream *rt) {
         }
     }
     if (status == XE_OK) {
-        for (cudaStream_t st : all) cudaStreamDestroy(st);
-        for (auto &ps : rt->streams)
-            for (Region &r : ps->regions) {
-                cudaEventDestroy(r.copied);
-                cudaEventDestroy(r.consumed);
-            }
-        cudaFree(rt->pool);
+        free_runtime(rt);
         delete rt;
     }
     return status;
