@@ -150,11 +150,22 @@ _L = _Lazy()
 # ----------------------------------------------------------------------------- marshalling helpers
 
 def _ptr(t):
+    """Address of a dense buffer: an int (a raw address) passes through; a tensor must be contiguous,
+    since every libxe buffer is a dense array in the layout include/xe.h states."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
+    if not t.is_contiguous():
+        raise ValueError("libxe buffers are dense arrays: pass a contiguous tensor")
     return t.data_ptr()
+
+
+def _dptr(t):
+    """As _ptr, for the buffers libxe's kernels read or write: a tensor must live on a CUDA device."""
+    if t is not None and not isinstance(t, int) and not t.is_cuda:
+        raise ValueError("libxe device arguments must be CUDA tensors (or raw device addresses)")
+    return _ptr(t)
 
 
 def _stream(stream):
@@ -205,7 +216,7 @@ def xe_selftest_timeout(timeout_ns: int, stream=None):
 
 def xe_probe_mma_legacy(kind: int, blocks: int, iters: int, sink, stream=None):
     """Rate probe of the legacy mma.sync path: kind 0 = m16n8k64 s4, 1 = m16n8k32 s8."""
-    _check(_L.xe_probe_mma_legacy(kind, blocks, iters, _ptr(sink), _stream(stream)), "xe_probe_mma_legacy")
+    _check(_L.xe_probe_mma_legacy(kind, blocks, iters, _dptr(sink), _stream(stream)), "xe_probe_mma_legacy")
 
 
 # ----------------------------------------------------------------------------- A1
@@ -216,8 +227,8 @@ def xe_assemble_workspace_size(shape: Shape) -> int:
 
 def xe_assemble(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
                 frame, filled, lost, stats, ws, stream=None):
-    _check(_L.xe_assemble(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(frame),
-                            _ptr(filled), _ptr(lost), _ptr(stats), _ptr(ws), _nbytes(ws), _stream(stream)),
+    _check(_L.xe_assemble(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _dptr(frame),
+                            _dptr(filled), _dptr(lost), _dptr(stats), _dptr(ws), _nbytes(ws), _stream(stream)),
            "xe_assemble")
 
 
@@ -230,14 +241,14 @@ def xe_assemble_noalloc(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_pe
     (stream capture, non-blocking real-time loops, hosts that own all device memory): the owner
     table is a fixed 1 MiB array inside libxe shared by every call, so calls must not overlap on the
     GPU, and frames with (T/4)*(F/8) above XE_ASSEMBLE_NOALLOC_MAX_SLOTS are rejected (XE_ENOMEM)."""
-    _check(_L.xe_assemble_noalloc(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(frame),
-                                  _ptr(filled), _ptr(lost), _ptr(stats), _stream(stream)), "xe_assemble_noalloc")
+    _check(_L.xe_assemble_noalloc(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _dptr(frame),
+                                  _dptr(filled), _dptr(lost), _dptr(stats), _stream(stream)), "xe_assemble_noalloc")
 
 
 # ----------------------------------------------------------------------------- A2..A4
 
 def xe_unpack(frame, shape: Shape, y, ldy: int, stream=None):
-    _check(_L.xe_unpack(_ptr(frame), shape, _ptr(y), ldy, _stream(stream)), "xe_unpack")
+    _check(_L.xe_unpack(_dptr(frame), shape, _dptr(y), ldy, _stream(stream)), "xe_unpack")
 
 
 def xe_correlate_workspace_size(shape: Shape) -> int:
@@ -245,7 +256,7 @@ def xe_correlate_workspace_size(shape: Shape) -> int:
 
 
 def xe_correlate(frame, shape: Shape, vis, accumulate: bool, ws, stream=None):
-    _check(_L.xe_correlate(_ptr(frame), shape, _ptr(vis), 1 if accumulate else 0, _ptr(ws), _nbytes(ws),
+    _check(_L.xe_correlate(_dptr(frame), shape, _dptr(vis), 1 if accumulate else 0, _dptr(ws), _nbytes(ws),
                              _stream(stream)), "xe_correlate")
 
 
@@ -255,7 +266,7 @@ def _jobs(jobs):
     for k, j in enumerate(jobs):
         frame, vis, shape, acc = j[:4]
         ms = j[4] if len(j) > 4 else 0
-        arr[k] = Job(_ptr(frame), _ptr(vis), shape, 1 if acc else 0, int(ms))
+        arr[k] = Job(_dptr(frame), _dptr(vis), shape, 1 if acc else 0, int(ms))
     return arr
 
 
@@ -275,7 +286,7 @@ def xe_correlate_batched_workspace_size(jobs, tune=None) -> int:
 def xe_correlate_batched(jobs, ws, tune=None, stream=None):
     """jobs: sequence of (frame, vis, Shape, accumulate)."""
     arr = _jobs(jobs)
-    _check(_L.xe_correlate_batched(arr, len(jobs), _tune(tune), _ptr(ws), _nbytes(ws), _stream(stream)),
+    _check(_L.xe_correlate_batched(arr, len(jobs), _tune(tune), _dptr(ws), _nbytes(ws), _stream(stream)),
            "xe_correlate_batched")
 
 
@@ -286,8 +297,8 @@ def xe_flag_counts_workspace_size(shape: Shape) -> int:
 def xe_flag_counts(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
                    flag_count, flag_pairs, ws, stream=None):
     """F-engine flags from the packets' footers: += per-input counts and pair intersections."""
-    _check(_L.xe_flag_counts(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(flag_count),
-                             _ptr(flag_pairs), _ptr(ws), _nbytes(ws), _stream(stream)), "xe_flag_counts")
+    _check(_L.xe_flag_counts(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _dptr(flag_count),
+                             _dptr(flag_pairs), _dptr(ws), _nbytes(ws), _stream(stream)), "xe_flag_counts")
 
 
 def xe_correlate_packets_workspace_size(shape: Shape) -> int:
@@ -297,8 +308,8 @@ def xe_correlate_packets_workspace_size(shape: Shape) -> int:
 def xe_correlate_packets(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
                          vis, accumulate: bool, filled, lost, stats, ws, stream=None):
     """Zero-copy assembly + correlation: the result of xe_assemble then xe_correlate, without the frame."""
-    _check(_L.xe_correlate_packets(_ptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _ptr(vis),
-                                   1 if accumulate else 0, _ptr(filled), _ptr(lost), _ptr(stats), _ptr(ws),
+    _check(_L.xe_correlate_packets(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _dptr(vis),
+                                   1 if accumulate else 0, _dptr(filled), _dptr(lost), _dptr(stats), _dptr(ws),
                                    _nbytes(ws), _stream(stream)), "xe_correlate_packets")
 
 
@@ -306,8 +317,8 @@ def xe_correlate_packets(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_p
 
 def xe_normalize(vis, shape: Shape, t_int: int, lost, out, n_out=None, flag_count=None, flag_pairs=None,
                  stream=None):
-    _check(_L.xe_normalize(_ptr(vis), shape, t_int, _ptr(lost), _ptr(flag_count), _ptr(flag_pairs), _ptr(out),
-                             _ptr(n_out), _stream(stream)), "xe_normalize")
+    _check(_L.xe_normalize(_dptr(vis), shape, t_int, _dptr(lost), _dptr(flag_count), _dptr(flag_pairs), _dptr(out),
+                             _dptr(n_out), _stream(stream)), "xe_normalize")
 
 
 # ----------------------------------------------------------------------------- A7

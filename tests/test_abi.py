@@ -3,6 +3,9 @@ import ctypes
 import os
 import re
 
+import pytest
+import torch
+
 import paper_1503_06189_b300 as xe
 
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "xe.h")
@@ -42,3 +45,15 @@ def test_host_only_calls():
                                                                  k_flush=0, n_ctas=0))
     assert unpacked >= 64 * 512 * 16384                           # + the E5M2 operand in HBM
     assert xe.xe_assemble_workspace_size(xe.Shape(256, 1024, 4096)) == 1024 * 128 * 4
+
+
+def test_binding_rejects_host_and_strided_buffers():
+    """The binding passes raw addresses, so it refuses what would reach the library in the wrong
+    place or layout: a host tensor where a device buffer is expected, and a non-contiguous view.
+    Both are caught before the library is called."""
+    with pytest.raises(ValueError, match="CUDA"):
+        xe.xe_correlate(torch.zeros(16, dtype=torch.uint8), xe.Shape(16, 1, 1),
+                        torch.zeros((1, xe.npairs(16), 2), dtype=torch.int32), False, None)
+    with pytest.raises(ValueError, match="contiguous"):
+        xe._ptr(torch.zeros((4, 8), dtype=torch.uint8).t())
+    assert xe._ptr(1 << 20) == 1 << 20 and xe._dptr(None) is None
