@@ -57,6 +57,40 @@ def unpack_triangle(vis, N):
     return out
 
 
+def assemble_by_definition(pkts, seq0, gps, N, F, T):
+    """Assembly written out from its definition (Sec. II-A) with Python integers, one packet at a
+    time in arrival order: header {u16 stream, u16 group, u32 reserved, u64 seq} little-endian, payload
+    [4 t][8 channels][N]; a foreign stream or group is invalid, seq below the window late, at or past
+    its end early; the first arrival of a (slot, group) is placed, later ones are duplicates; slots
+    nothing filled stay zero and count 4 lost samples on each of the group's channels."""
+    G, Q = F // 8, T // 4
+    S = G // gps
+    frame = np.zeros((T, F, N), np.uint8)
+    filled = np.zeros((Q, G), np.uint8)
+    stats = [0, 0, 0, 0, 0]                                          # ok, duplicate, late, early, invalid
+    for rec in pkts:
+        h = bytes(rec[:16])
+        sid, grp = int.from_bytes(h[0:2], "little"), int.from_bytes(h[2:4], "little")
+        seq = int.from_bytes(h[8:16], "little")
+        if sid >= S or grp >= gps:
+            stats[4] += 1
+        elif seq < seq0:
+            stats[2] += 1
+        elif seq >= seq0 + Q:
+            stats[3] += 1
+        elif filled[seq - seq0, sid * gps + grp]:
+            stats[1] += 1
+        else:
+            slot, g = seq - seq0, sid * gps + grp
+            frame[4 * slot:4 * slot + 4, 8 * g:8 * g + 8, :] = np.asarray(rec[16:16 + 32 * N]).reshape(4, 8, N)
+            filled[slot, g] = 1
+            stats[0] += 1
+    lost = np.zeros(F, np.uint32)
+    for g in range(G):
+        lost[8 * g:8 * g + 8] = 4 * (Q - int(filled[:, g].sum()))
+    return frame, filled, lost, np.array(stats, np.uint32)
+
+
 # ----------------------------------------------------------------------------- pins (take an oracle)
 
 def pin_sample_decode(o):
@@ -259,6 +293,29 @@ def pin_assembly_window(o):
     assert not out[12:].any()
 
 
+def pin_assembly_random_by_definition(o, cases=40):
+    """Random packet sets assemble exactly as the definition written out packet by packet: valid,
+    late, early, foreign-stream and foreign-group packets, and same-slot duplicates carrying different
+    payloads, in random arrival order, with 64-bit sequence numbers."""
+    rng = np.random.default_rng(26)
+    for _ in range(cases):
+        N = int(rng.choice([16, 32]))
+        gps, S, Q = int(rng.integers(1, 3)), int(rng.integers(1, 4)), int(rng.integers(1, 9))
+        F, T = 8 * S * gps, 4 * Q
+        seq0 = int(rng.integers(3, 1 << 40))
+        n = int(rng.integers(0, 3 * Q * S * gps + 1))
+        pk = np.zeros((n, 16 + 32 * N), np.uint8)
+        for k in range(n):
+            sid = int(rng.integers(0, S + 1)) if rng.random() < 0.9 else int(rng.integers(S, 1 << 16))
+            grp = int(rng.integers(0, gps)) if rng.random() < 0.95 else gps
+            pk[k, :16] = synth.make_header(sid, grp, seq0 + int(rng.integers(-3, Q + 3)))
+            pk[k, 16:] = rng.integers(0, 256, 32 * N, dtype=np.uint8)
+        got = o.assemble(pk, seq0, gps, N, F, T)
+        want = assemble_by_definition(pk, seq0, gps, N, F, T)
+        for name, a, b in zip(("frame", "filled", "lost", "stats"), got, want):
+            np.testing.assert_array_equal(a, b, err_msg=name)
+
+
 def pin_counts_counters_equal_mask(o):
     """The paper's counter scheme (loss counter, per-input flag counts, pair intersections) gives the
     same per-visibility sample counts as brute force over the sample mask."""
@@ -391,6 +448,7 @@ def pin_flag_counts_give_mask_counts(o):
 PINS = [pin_sample_decode, pin_pidx_bijection, pin_brute_force, pin_pairs, pin_library_gram, pin_subset_channels,
         pin_autocorrelation, pin_constant_input, pin_single_source, pin_overflow_bound,
         pin_assembly_basic, pin_assembly_permutation, pin_assembly_loss_and_dups, pin_assembly_window,
+        pin_assembly_random_by_definition,
         pin_counts_counters_equal_mask, pin_normalize, pin_table1_geometry, pin_flag_footer_layout,
         pin_flag_counts_brute_force, pin_flag_counts_give_mask_counts]
 
