@@ -220,6 +220,23 @@ def packet_stream(frame: np.ndarray, seq0: int, groups_per_stream: int, seed: in
     return np.ascontiguousarray(pk[order])
 
 
+def random_packet_set(seed: int, n_inputs: int, n_streams: int, groups_per_stream: int, n_slots: int,
+                      n_packets: int, seq0: int) -> np.ndarray:
+    """Packets with random headers and random payloads, in random arrival order: mostly valid
+    (stream < n_streams, group < groups_per_stream, seq in [seq0, seq0 + n_slots)), some late
+    (seq0 - 3 .. seq0 - 1) or early (up to seq0 + n_slots + 2), about 10 % from foreign streams (up to
+    65535) and 5 % with a foreign group. Slots drawn twice become duplicates with different payloads.
+    uint8 [n_packets][16 + 32 N]; requires seq0 >= 3."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pk = np.zeros((n_packets, packet_stride(n_inputs)), dtype=np.uint8)
+    for k in range(n_packets):
+        sid = int(rng.integers(0, n_streams + 1)) if rng.random() < 0.9 else int(rng.integers(n_streams, 1 << 16))
+        grp = int(rng.integers(0, groups_per_stream)) if rng.random() < 0.95 else groups_per_stream
+        pk[k, :HEADER_BYTES] = make_header(sid, grp, seq0 + int(rng.integers(-3, n_slots + 3)))
+        pk[k, HEADER_BYTES:] = rng.integers(0, 256, payload_bytes(n_inputs), dtype=np.uint8)
+    return pk
+
+
 def packetize_torch(frame, seq0: int, groups_per_stream: int):
     """Torch twin of :func:`packetize` (runs where ``frame`` lives). Returns uint8 [n][16+32N]."""
     import torch

@@ -65,6 +65,36 @@ def test_packets_match_oracle(N, F, T, gps, p_drop, p_reorder, p_dup):
     assert stats_o[2] > 0 and stats_o[3] > 0                # late and early packets were present
 
 
+def test_random_packet_sets_with_64_bit_sequence_numbers():
+    """Random packet sets whose sequence numbers lie far beyond 2^32 (the header's seq is a u64):
+    valid, late, early, foreign-stream and foreign-group packets, and duplicates carrying different
+    payloads, in random arrival order. xe_assemble and xe_correlate_packets both match the oracle's
+    assembly (and its correlation of that frame) bit for bit."""
+    rng = np.random.default_rng(27)
+    for case in range(12):
+        N = int(rng.choice([16, 32, 64]))
+        gps, S, Q = int(rng.integers(1, 3)), int(rng.integers(1, 4)), int(rng.integers(1, 40))
+        F, T = 8 * S * gps, 4 * Q
+        seq0 = int(rng.integers(1 << 33, 1 << 50))
+        n = int(rng.integers(1, 3 * Q * S * gps + 1))
+        pk = synth.random_packet_set(270 + case, N, S, gps, Q, n, seq0)
+        frame_o, filled_o, lost_o, stats_o = oracle.assemble(pk, seq0, gps, N, F, T)
+        vis_o, st = oracle.correlate(frame_o)
+        assert st == oracle.OK
+        s = xe.Shape(N, F, T)
+        frame = torch.full((T, F, N), 0xA5, dtype=torch.uint8, device="cuda")
+        filled = torch.full((Q, F // 8), 7, dtype=torch.uint8, device="cuda")
+        lost = torch.zeros(F, dtype=torch.int32, device="cuda")
+        stats = torch.zeros(5, dtype=torch.int32, device="cuda")
+        ws = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device="cuda")
+        xe.xe_assemble(X.dev(pk), n, pk.shape[1], seq0, gps, s, frame, filled, lost, stats, ws)
+        np.testing.assert_array_equal(_host(frame), frame_o, err_msg=f"case {case}: frame")
+        for name, got, want in (("filled", filled, filled_o), ("lost", lost, lost_o), ("stats", stats, stats_o)):
+            np.testing.assert_array_equal(_host(got, np.uint32), np.asarray(want, np.uint32), err_msg=f"case {case}: {name}")
+        vis, filled2, lost2, stats2 = _packets_gpu(pk, seq0, gps, N, F, T)
+        np.testing.assert_array_equal(_host(vis, np.int64), vis_o, err_msg=f"case {case}: zero-copy vis")
+        assert torch.equal(filled2, filled) and torch.equal(lost2, lost) and torch.equal(stats2, stats)
+
 def test_packets_accumulate_over_two_frames():
     """Two consecutive frames of one stream integrate into one visibility set; lost and stats
     accumulate like xe_assemble's."""

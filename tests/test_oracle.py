@@ -298,18 +298,13 @@ def pin_assembly_random_by_definition(o, cases=40):
     late, early, foreign-stream and foreign-group packets, and same-slot duplicates carrying different
     payloads, in random arrival order, with 64-bit sequence numbers."""
     rng = np.random.default_rng(26)
-    for _ in range(cases):
+    for case in range(cases):
         N = int(rng.choice([16, 32]))
         gps, S, Q = int(rng.integers(1, 3)), int(rng.integers(1, 4)), int(rng.integers(1, 9))
         F, T = 8 * S * gps, 4 * Q
         seq0 = int(rng.integers(3, 1 << 40))
         n = int(rng.integers(0, 3 * Q * S * gps + 1))
-        pk = np.zeros((n, 16 + 32 * N), np.uint8)
-        for k in range(n):
-            sid = int(rng.integers(0, S + 1)) if rng.random() < 0.9 else int(rng.integers(S, 1 << 16))
-            grp = int(rng.integers(0, gps)) if rng.random() < 0.95 else gps
-            pk[k, :16] = synth.make_header(sid, grp, seq0 + int(rng.integers(-3, Q + 3)))
-            pk[k, 16:] = rng.integers(0, 256, 32 * N, dtype=np.uint8)
+        pk = synth.random_packet_set(260 + case, N, S, gps, Q, n, seq0)
         got = o.assemble(pk, seq0, gps, N, F, T)
         want = assemble_by_definition(pk, seq0, gps, N, F, T)
         for name, a, b in zip(("frame", "filled", "lost", "stats"), got, want):
