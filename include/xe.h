@@ -98,18 +98,18 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
 
 /*
  * Allocation-free variant of xe_assemble. The paper has no counterpart to this call: it exists for
- * callers that cannot allocate device memory where they assemble frames -- for example code that
- * runs while a stream is being captured into a CUDA graph (cudaMalloc is not a stream operation
- * and cannot be captured), real-time receive loops that must not block (cudaMalloc can synchronise
- * the device and stall for milliseconds), or plug-ins whose host application owns every device
- * allocation and hands out no scratch space.
+ * callers that cannot allocate device memory where they assemble frames -- real-time receive loops
+ * that must not block (cudaMalloc can synchronise the device and stall for milliseconds), or
+ * plug-ins whose host application owns every device allocation and hands out no scratch space.
  *
  * Arguments and results are those of xe_assemble, without the workspace: the owner table lives in
  * a static array inside libxe of XE_ASSEMBLE_NOALLOC_MAX_SLOTS entries (1 MiB per device that loads
  * the library, held until the process exits). A frame may use at most that many (slot, group)
  * pairs, (T/4) * (F/8) <= XE_ASSEMBLE_NOALLOC_MAX_SLOTS; larger frames return XE_ENOMEM.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture. The call allocates nothing. All calls share the one array
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); so does the first call after the device's context has been reset, since the
+ * array then lives at a new address. Make that first call before any stream capture; a call with
+ * n_pkts = 0 on a small shape serves. The call allocates nothing. All calls share the one array
  * and each call resets the part it uses, so calls whose kernels may overlap on the GPU (different
  * streams, or overlapping graph nodes) race and must be serialised by the caller.
  */
@@ -322,14 +322,17 @@ typedef struct {
     uint32_t packets;           /* packets submitted into this frame's region */
     uint32_t batch;             /* admission round that carried the frame */
     uint64_t latency_ns;        /* frame closed -> its results complete on the device */
+    uint64_t latency_submit_ns; /* submission of the frame's last packet -> results complete (includes
+                                   the wait for the reorder window to close the frame) */
 } xe_result;
 
 typedef struct {
     uint64_t packets_submitted, packets_late, frames_closed, frames_done, frames_released;
     uint64_t batches, max_batch_seen;
-    double latency_p50_us, latency_p99_us, latency_max_us;
+    double latency_p50_us, latency_p99_us, latency_max_us;              /* close -> complete */
     uint64_t device_bytes;
     int32_t slots;
+    double latency_submit_p50_us, latency_submit_p99_us, latency_submit_max_us;   /* last packet -> complete */
 } xe_stream_stats_t;
 
 /* Creates the runtime on the current device. Errors: XE_EINVAL, XE_ENOMEM (budget too small for
@@ -337,10 +340,20 @@ typedef struct {
 int xe_stream_create(const xe_stream_cfg *cfg, xe_stream **out);
 /* Submits n_pkts packets (host memory, arrival order) of one stream. Packets of closed frames count
  * as late and are dropped. Returns XE_EAGAIN, having consumed nothing, when a packet belongs to a
- * frame whose packet region is still in use (the device is behind): retry later. Pinned host
+ * frame whose packet region is still in use, or when frames must close and the queue of closed
+ * frames is full (the device or the consumer is behind): poll, release and retry. Pinned host
  * memory is copied asynchronously: keep it unchanged until the frames it holds have completed. */
 int xe_stream_submit(xe_stream *s, int32_t stream_id, const void *host_pkts, uint32_t n_pkts);
-/* Closes every open frame (end of data). */
+/* As xe_stream_submit for packets already in device memory (for example written there by a NIC,
+ * with the headers also delivered to the host, or replayed from a device ring): dev_pkts holds
+ * n_pkts records of pkt_stride bytes on the runtime's device, host_headers the same packets' 16-byte
+ * headers back to back in host memory (read during the call, to route each packet to its frame).
+ * The records are copied device to device into the frames' packet regions; keep dev_pkts unchanged
+ * until the frames it holds have completed. */
+int xe_stream_submit_device(xe_stream *s, int32_t stream_id, const void *dev_pkts, const void *host_headers,
+                            uint32_t n_pkts);
+/* Closes every open frame (end of data). XE_EAGAIN if the queue of closed frames filled up first:
+ * poll, release and call it again. */
 int xe_stream_flush(xe_stream *s);
 /* Waits up to timeout_ms for the next completed frame (completion order). XE_ETIMEOUT if none. */
 int xe_stream_poll(xe_stream *s, xe_result *out, int32_t timeout_ms);

@@ -28,7 +28,7 @@ EXPORTED = [
     "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched",
     "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_flag_counts_workspace_size",
     "xe_flag_counts", "xe_normalize", "xe_probe_mma_legacy",
-    "xe_stream_create", "xe_stream_submit", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
+    "xe_stream_create", "xe_stream_submit", "xe_stream_submit_device", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
     "xe_stream_stats", "xe_stream_destroy",
 ]
 
@@ -74,7 +74,7 @@ class Result(ctypes.Structure):
     _fields_ = [("stream_id", ctypes.c_int32), ("slot", ctypes.c_int32), ("frame", ctypes.c_int64),
                 ("out", ctypes.c_void_p), ("vis", ctypes.c_void_p), ("n", ctypes.c_void_p),
                 ("lost", ctypes.c_void_p), ("stats", ctypes.c_void_p), ("packets", ctypes.c_uint32),
-                ("batch", ctypes.c_uint32), ("latency_ns", ctypes.c_uint64)]
+                ("batch", ctypes.c_uint32), ("latency_ns", ctypes.c_uint64), ("latency_submit_ns", ctypes.c_uint64)]
 
 
 class StreamStats(ctypes.Structure):
@@ -83,7 +83,9 @@ class StreamStats(ctypes.Structure):
                 ("frames_released", ctypes.c_uint64), ("batches", ctypes.c_uint64),
                 ("max_batch_seen", ctypes.c_uint64), ("latency_p50_us", ctypes.c_double),
                 ("latency_p99_us", ctypes.c_double), ("latency_max_us", ctypes.c_double),
-                ("device_bytes", ctypes.c_uint64), ("slots", ctypes.c_int32)]
+                ("device_bytes", ctypes.c_uint64), ("slots", ctypes.c_int32),
+                ("latency_submit_p50_us", ctypes.c_double), ("latency_submit_p99_us", ctypes.c_double),
+                ("latency_submit_max_us", ctypes.c_double)]
 
 
 def _load():
@@ -118,6 +120,7 @@ def _load():
     L.xe_normalize.argtypes = [vp, Shape, u32, vp, vp, vp, vp, vp, vp]
     L.xe_stream_create.argtypes = [ctypes.POINTER(StreamCfg), ctypes.POINTER(vp)]
     L.xe_stream_submit.argtypes = [vp, i32, vp, u32]
+    L.xe_stream_submit_device.argtypes = [vp, i32, vp, vp, u32]
     L.xe_stream_flush.argtypes = [vp]
     L.xe_stream_poll.argtypes = [vp, ctypes.POINTER(Result), i32]
     L.xe_stream_release.argtypes = [vp, ctypes.POINTER(Result)]
@@ -238,9 +241,9 @@ XE_ASSEMBLE_NOALLOC_MAX_SLOTS = 1 << 18
 def xe_assemble_noalloc(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int, shape: Shape,
                         frame, filled, lost, stats, stream=None):
     """xe_assemble without a workspace, for callers that cannot allocate device memory at this point
-    (stream capture, non-blocking real-time loops, hosts that own all device memory): the owner
-    table is a fixed 1 MiB array inside libxe shared by every call, so calls must not overlap on the
-    GPU, and frames with (T/4)*(F/8) above XE_ASSEMBLE_NOALLOC_MAX_SLOTS are rejected (XE_ENOMEM)."""
+    (non-blocking real-time loops, hosts that own all device memory): the owner table is a fixed
+    1 MiB array inside libxe shared by every call, so calls must not overlap on the GPU, and frames
+    with (T/4)*(F/8) above XE_ASSEMBLE_NOALLOC_MAX_SLOTS are rejected (XE_ENOMEM)."""
     _check(_L.xe_assemble_noalloc(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _dptr(frame),
                                   _dptr(filled), _dptr(lost), _dptr(stats), _stream(stream)), "xe_assemble_noalloc")
 
@@ -342,8 +345,23 @@ def xe_stream_submit(handle, stream_id: int, host_pkts, n_pkts: int) -> int:
     return st
 
 
-def xe_stream_flush(handle):
-    _check(_L.xe_stream_flush(handle), "xe_stream_flush")
+def xe_stream_submit_device(handle, stream_id: int, dev_pkts, host_headers, n_pkts: int) -> int:
+    """dev_pkts: device records (CUDA tensor or address); host_headers: their 16-byte headers back to
+    back in host memory (numpy/torch CPU buffer or address). Returns XE_OK or XE_EAGAIN."""
+    hdr = host_headers.ctypes.data if hasattr(host_headers, "ctypes") else _ptr(host_headers)
+    st = _L.xe_stream_submit_device(handle, stream_id, _dptr(dev_pkts), hdr, n_pkts)
+    if st not in (XE_OK, XE_EAGAIN):
+        raise XeError(st, "xe_stream_submit_device")
+    return st
+
+
+def xe_stream_flush(handle) -> int:
+    """Closes every open frame; XE_EAGAIN if the queue of closed frames filled first (poll, release,
+    call again)."""
+    st = _L.xe_stream_flush(handle)
+    if st not in (XE_OK, XE_EAGAIN):
+        raise XeError(st, "xe_stream_flush")
+    return st
 
 
 def xe_stream_poll(handle, timeout_ms: int):

@@ -358,23 +358,57 @@ namespace asmb {
 
 static __device__ __align__(256) uint32_t g_noalloc_owner[XE_ASSEMBLE_NOALLOC_MAX_SLOTS];
 
-// Device address of g_noalloc_owner on the current device, resolved once per device. In host code
-// the symbol itself is only a host-side stand-in, so the kernels must be given this address.
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+// Identity of the current device's context (0 if there is none yet). A context id is unique for the
+// life of the process, so a context created after a device reset gets a new one.
+static unsigned long long current_ctx_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of g_noalloc_owner on the current device. In host code the symbol itself is only a
+// host-side stand-in, so the kernels must be given this address. It is looked up with the device
+// current on the first call in each of the device's contexts (the first call after cudaDeviceReset
+// looks it up again: the array then lives at a new address) and cached against the context's id.
 static uint32_t *noalloc_owner(int *status) {
-    static uint32_t *addr[64] = {};
+    struct Entry {
+        unsigned long long ctx = 0;
+        uint32_t *addr = nullptr;
+    };
+    static Entry cache[64];
     static std::mutex mu;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { *status = cuda_fail(e); return nullptr; }
     if (dev < 0 || dev >= 64) { *status = XE_EINVAL; return nullptr; }
     std::lock_guard<std::mutex> lock(mu);
-    if (!addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_owner);
-        if (e != cudaSuccess || !p) { *status = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol); return nullptr; }
-        addr[dev] = static_cast<uint32_t *>(p);
-    }
-    return addr[dev];
+    unsigned long long ctx = current_ctx_id();
+    if (ctx != 0 && cache[dev].ctx == ctx && cache[dev].addr) return cache[dev].addr;
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_owner);       // creates the context if there is none yet
+    if (e != cudaSuccess || !p) { *status = cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol); return nullptr; }
+    if (ctx == 0) ctx = current_ctx_id();
+    cache[dev].ctx = ctx;
+    cache[dev].addr = static_cast<uint32_t *>(p);
+    return cache[dev].addr;
 }
 
 }  // namespace asmb
@@ -383,38 +417,15 @@ static uint32_t *noalloc_owner(int *status) {
 extern "C" int xe_assemble_noalloc(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
                                    int32_t gps, xe_shape s, uint8_t *frame, uint8_t *filled, uint32_t *lost,
                                    uint32_t *stats, void *stream) {
-    if (!valid_shape(s) || s.n_time < 4 || s.n_time % 4 || s.n_chan % 8 || gps < 1 || (s.n_chan / 8) % gps)
-        return XE_EINVAL;
-    if (!frame || !filled || !lost || !stats || (n_pkts && !pkts)) return XE_EINVAL;
-    if (pkt_stride % 16 || pkt_stride < 16u + 32u * (uint32_t)s.n_inputs) return XE_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(pkts) | reinterpret_cast<uintptr_t>(frame)) & 15) return XE_EINVAL;
-    if ((reinterpret_cast<uintptr_t>(lost) | reinterpret_cast<uintptr_t>(stats)) & 3) return XE_EINVAL;
-    const int64_t slots = (int64_t)(s.n_time / 4) * (s.n_chan / 8);
+    asmb::Geo g;
+    if (int e = asmb::make_geo(pkts, n_pkts, pkt_stride, seq0, gps, 0, s, filled, lost, stats, g)) return e;
+    if (!frame || (reinterpret_cast<uintptr_t>(frame) & 15)) return XE_EINVAL;
+    const int64_t slots = (int64_t)g.Q * g.G;
     if (slots > XE_ASSEMBLE_NOALLOC_MAX_SLOTS) return XE_ENOMEM;    // frame larger than the static table
     int status = XE_OK;
     uint32_t *owner = asmb::noalloc_owner(&status);
     if (!owner) return status;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    asmb::Geo g;
-    g.seq0 = seq0;
-    g.n_pkts = n_pkts;
-    g.stride = pkt_stride;
-    g.N = s.n_inputs;
-    g.F = s.n_chan;
-    g.Q = s.n_time / 4;
-    g.G = s.n_chan / 8;
-    g.gps = gps;
-    g.S = g.G / gps;
-    // The table keeps whatever the previous call left in it: reset the slots this frame uses.
-    asmb::init_kernel<<<(unsigned)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, st>>>(owner, slots);
-    XE_TRY_CUDA(cudaGetLastError());
-    if (n_pkts) {
-        asmb::claim_kernel<<<(n_pkts + 255) / 256, 256, 0, st>>>(pkts, g, owner, stats, 0);
-        XE_TRY_CUDA(cudaGetLastError());
-    }
-    const uint64_t blocks = ((uint64_t)n_pkts + (uint64_t)slots + 3) / 4;
-    if (blocks > 0x7FFFFFFFull) return XE_EINVAL;
-    asmb::copy_kernel<<<(unsigned)blocks, asmb::kCopyThreads, 0, st>>>(pkts, g, owner, frame, filled, lost, stats);
-    XE_TRY_CUDA(cudaGetLastError());
-    return XE_OK;
+    // the table keeps whatever the previous call left in it: launch() first resets the slots this
+    // frame uses (init), then claims and copies exactly as xe_assemble does
+    return asmb::launch<true>(pkts, g, owner, frame, filled, lost, stats, static_cast<cudaStream_t>(stream));
 }

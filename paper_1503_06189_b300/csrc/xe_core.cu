@@ -120,7 +120,7 @@ const char *xe_strerror(int status) {
 
 int xe_last_cuda_error(void) { return xe::t_last_cuda; }
 
-int xe_version(void) { return 10000; }
+int xe_version(void) { return 10100; }
 
 int xe_device_status(int *status_out, void *stream) {
     if (!status_out) return XE_EINVAL;

@@ -1,8 +1,8 @@
 """xe_assemble_noalloc against xe_assemble (GPU, through the C ABI).
 
 The allocation-free entry point serves callers that cannot allocate device memory where they
-assemble frames (inside stream capture, in non-blocking receive loops, or under a host that owns all
-device memory); its scratch is a fixed array inside the library that every call reuses. This file is
+assemble frames (non-blocking receive loops, or a host that owns all device memory); its scratch
+is a fixed array inside the library that every call reuses. This file is
 collected last on purpose, so that a run stopping at its first failure has run everything else. The
 checks: two calls in a row on different packet sets must each give exactly what the workspace entry
 point gives (assembly is integer work: bit-exact), the second call must not see leftovers of the
