@@ -165,40 +165,76 @@ def run_reference(args):
     return 0
 
 
-def run_serving(xe, torch, dev, frames_per_stream: int = 8, seed: int = 5000, ring_frames: int = 6):
-    """Configuration 5: 8 F-engine streams x 128 channels (16 groups of 8), N = 256, T = 4096 per
-    frame, 16-byte-header packets with 8 KiB payloads arriving as Poisson processes totalling 819.2
-    Gb/s of payload (12.5 M packets/s), 0.1% dropped, 0.5% reordered (displacement 1..64), submitted
-    from pinned host memory into the serving loop (xe_stream_*). Reports the achieved rate and the
-    p50 / p99 latency from frame close to its normalised visibilities being complete."""
+def make_serving_packets(torch, dev, frames_per_stream: int = 8, seed: int = 5000):
+    """Configuration 5's packets: 8 F-engine streams x 128 channels (16 groups of 8), N = 256, T = 4096
+    per frame, 16-byte-header packets with 8 KiB payloads, 0.1% dropped, 0.5% reordered (displacement
+    1..64). Returns, per stream, the packets in arrival order in pinned host memory and in device
+    memory, and their headers in host memory."""
     import numpy as np
 
     import synth
 
     S, GPS, N, T = 8, 16, 256, 4096
-    Fs, Q = 8 * GPS, T // 4
-    stride = synth.packet_stride(N)
-    rng = np.random.default_rng(seed)
-    host = []
+    host, devp, hdrs = [], [], []
     for s in range(S):
-        fr = synth.signal_frame_torch(N, Fs, T * frames_per_stream, seed + s, device=dev, chunk=32)
+        fr = synth.signal_frame_torch(N, 8 * GPS, T * frames_per_stream, seed + s, device=dev, chunk=32)
         pk = synth.packetize_torch(fr, 0, GPS)
         del fr
         pk[:, 0:2] = torch.tensor(list(np.uint16(s).tobytes()), dtype=torch.uint8, device=dev)
         order = synth.network_order(pk.shape[0], seed + 100 + s, p_drop=0.001, p_reorder=0.005)
-        pk = pk[torch.from_numpy(order).to(dev)]
+        pk = pk[torch.from_numpy(order).to(dev)].contiguous()
         h = torch.empty(pk.shape, dtype=torch.uint8).pin_memory()
         h.copy_(pk)
         host.append(h)
-        del pk
+        devp.append(pk)
+        hdrs.append(np.ascontiguousarray(h[:, :16].numpy()))
     torch.cuda.synchronize(dev)
-    rate = 12.5e6 / S                                  # packets/s per stream
-    arrive = [np.cumsum(rng.exponential(1.0 / rate, h.shape[0])) for h in host]
+    return host, devp, hdrs
+
+
+def link_gbs(torch, dev, nbytes: int = 1 << 30) -> float:
+    """Pinned host -> device copy rate (GB/s) of this machine's host link, best of 3."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        d.copy_(h, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        best = max(best, nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    del h, d
+    return best
+
+
+def run_serving(xe, torch, dev, pk, offered_gbps, feed: str = "host", seed: int = 5000, ring_frames: int = 6):
+    """Configuration 5 through xe_stream_*: the 8 streams' packets arrive as Poisson processes
+    totalling `offered_gbps` of payload (None: as fast as the producer loop submits them), from
+    pinned host memory (feed "host": H2D copies) or from device memory (feed "device": D2D copies,
+    headers read from a host copy). Reports the achieved payload rate and the p50 / p99 latency of a
+    frame from its close, and from the submission of its last packet, to its normalised visibilities
+    being complete."""
+    import numpy as np
+
+    import synth
+
+    host, devp, hdrs = pk
+    S, GPS, N, T = 8, 16, 256, 4096
+    stride = synth.packet_stride(N)
+    frames_per_stream = host[0].shape[0] // (T // 4 * GPS)
+    rng = np.random.default_rng(seed)
+    if offered_gbps:
+        rate = offered_gbps * 1e9 / 8 / synth.payload_bytes(N) / S         # packets/s per stream
+        arrive = [np.cumsum(rng.exponential(1.0 / rate, h.shape[0])) for h in host]
+    else:
+        arrive = [np.zeros(h.shape[0]) for h in host]
     cfg = xe.StreamCfg(S, GPS, N, T, stride, 1024, ring_frames, 16, 8, 2, 0, 500)
     handle = xe.xe_stream_create(cfg)
     pos = [0] * S
     done = 0
     total = S * frames_per_stream
+    flushed = False
     t0 = time.perf_counter()
     try:
         while done < total:
@@ -210,12 +246,16 @@ def run_serving(xe, torch, dev, frames_per_stream: int = 8, seed: int = 5000, ri
                 hi = int(np.searchsorted(arrive[s], now, side="right"))
                 while pos[s] < hi:
                     n = min(4096, hi - pos[s])
-                    ptr = host[s].data_ptr() + pos[s] * stride
-                    if xe.xe_stream_submit(handle, s, ptr, n) != xe.XE_OK:
+                    if feed == "host":
+                        st = xe.xe_stream_submit(handle, s, host[s].data_ptr() + pos[s] * stride, n)
+                    else:
+                        st = xe.xe_stream_submit_device(handle, s, devp[s].data_ptr() + pos[s] * stride,
+                                                        hdrs[s][pos[s]:pos[s] + n], n)
+                    if st != xe.XE_OK:
                         break
                     pos[s] += n
-            if all(p >= h.shape[0] for p, h in zip(pos, host)):
-                xe.xe_stream_flush(handle)
+            if not flushed and all(p >= h.shape[0] for p, h in zip(pos, host)):
+                flushed = xe.xe_stream_flush(handle) == xe.XE_OK
             r = xe.xe_stream_poll(handle, 0)
             while r is not None:
                 xe.xe_stream_release(handle, r)
@@ -228,13 +268,36 @@ def run_serving(xe, torch, dev, frames_per_stream: int = 8, seed: int = 5000, ri
     finally:
         xe.xe_stream_destroy(handle)
     payload = sum(int(p) for p in pos) * synth.payload_bytes(N)
-    return {"workload": "8 streams x 128 ch, N=256, T=4096, Poisson arrivals at 819.2 Gb/s offered, "
-                        "0.1% drops, 0.5% reorders, pinned host packets -> xe_stream_*",
-            "frames": int(st.frames_done), "offered_gbps": 819.2,
+    return {"feed": feed, "offered_gbps": offered_gbps, "frames": int(st.frames_done),
             "achieved_gbps": payload * 8 / wall / 1e9, "wall_s": wall,
             "latency_p50_ms": st.latency_p50_us / 1e3, "latency_p99_ms": st.latency_p99_us / 1e3,
-            "latency_max_ms": st.latency_max_us / 1e3, "rounds": int(st.batches),
-            "max_frames_per_round": int(st.max_batch_seen), "device_bytes": int(st.device_bytes)}
+            "latency_max_ms": st.latency_max_us / 1e3,
+            "latency_from_last_packet_p50_ms": st.latency_submit_p50_us / 1e3,
+            "latency_from_last_packet_p99_ms": st.latency_submit_p99_us / 1e3,
+            "rounds": int(st.batches), "max_frames_per_round": int(st.max_batch_seen),
+            "device_bytes": int(st.device_bytes)}
+
+
+def run_serving_suite(xe, torch, dev):
+    """Configuration 5 at offered loads of 25 / 50 / 80 % of the measured host link, at the paper's
+    819.2 Gb/s from host memory (above the link), and from device memory at 819.2 Gb/s and unpaced
+    (the loop's own ceiling)."""
+    link = link_gbs(torch, dev)
+    pk = make_serving_packets(torch, dev)
+    link_payload_gbps = link * 8 * 8192 / 8208                     # payload share of the records
+    rows = []
+    for frac in (0.25, 0.5, 0.8):
+        r = run_serving(xe, torch, dev, pk, round(frac * link_payload_gbps, 1), "host")
+        r["offered_fraction_of_link"] = frac
+        rows.append(r)
+    rows.append(run_serving(xe, torch, dev, pk, 819.2, "host"))
+    rows.append(run_serving(xe, torch, dev, pk, 819.2, "device"))
+    rows.append(run_serving(xe, torch, dev, pk, None, "device"))
+    del pk
+    torch.cuda.empty_cache()
+    return {"workload": "8 streams x 128 ch, N=256, T=4096 (8 frames per stream), Poisson arrivals, 0.1% drops, "
+                        "0.5% reorders -> xe_stream_* (index + batched correlation + normalise per round)",
+            "host_link_gbs": link, "runs": rows}
 
 
 def workload_config(args):
@@ -422,7 +485,7 @@ def run_xe(args):
     serving = None
     if not args.no_serving:
         try:
-            serving = run_serving(xe, torch, dev)
+            serving = run_serving_suite(xe, torch, dev)
         except Exception as exc:
             serving = {"error": str(exc)}
 

@@ -75,6 +75,7 @@ struct Job {                 // 128-byte aligned through its CUtensorMap
     int32_t doubles;         // pair engine: double items per channel (0: every block a single item)
     int32_t offdiag;         // pair engine, packet mode: blocks (R, C >= R + 2) per channel
     int32_t twin;            // pair engine: 1 = packet-mode item layout (doubles, singles, twins)
+    int32_t fold;            // pair engine, packet mode: 1 = fold layout (see decode_pair_item)
 };
 
 struct Params {
@@ -83,6 +84,7 @@ struct Params {
     int32_t k_flush_tiles_wide;   // drain interval in wide stages (packet mode), else k_flush_tiles
     int32_t wide_diag;            // 1: single diagonal items run in wide stages (packet mode)
     int32_t op_stages, pk_stages, slots, n_acc;
+    int32_t fold;                 // some job has the fold layout: three operand slots, transpose staging
     int *status;
     int *counter;            // work-item counter, zero at launch
     uint64_t limit_ns;
@@ -639,8 +641,13 @@ __global__ void __launch_bounds__(Cfg<kEngine>::kThreads, 1) correlate_kernel(co
 // warp on different roles run their branches in turn, and a lane suspended in an mbarrier wait
 // would hold up the lane it waits for.
 
-constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA: A, B (a twin: A of channels
-                                              // f and f + 1; a wide stage: A, samples kKt further on)
+constexpr int kPairSlots = 2;                 // operand blocks per stage and CTA of Gram items: A, B (a twin: A
+                                              // of channels f and f + 1; a wide stage: A, samples kKt further on)
+constexpr int kFoldSlots = 3;                 // operand blocks per stage and CTA of fold items: S, A, B
+constexpr int kFoldStageD = 32 * 128 * 4;     // fold epilogue: 32 rows of this CTA's diagonal quadrant
+constexpr int kFoldStageX = 32 * 128 * 4;     // fold epilogue: 32 rows of the partner's off-diagonal quadrant
+constexpr int kFoldStageBytes = kFoldStageD + kFoldStageX;   // leaves room for four operand stages
+constexpr uint32_t kEpiBar = 1;               // named barrier of the four epilogue warps
 constexpr int kPairEpiWarps = 4;              // one per TMEM lane quarter (accumulator double-buffered)
 constexpr int kPairConvFwdWarp = 2;           // forwards converter completion, prefetches into L2
 constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
@@ -664,61 +671,107 @@ struct PairShape {
     static_assert(kRowStep % 8 == 0, "a thread's rows share their 128-byte swizzle phase");
 };
 constexpr int kPairMaxStages = 6;
+constexpr int kPairSmemBudget = 196 * 1024;   // dynamic shared memory of a pair CTA (see run_batched)
 // Packet mode: integrations of at least this many samples run the twin layout (see decode_pair_item)
 constexpr int kTwinMinTime = 16384;
 constexpr int kPairPrefetch = 4;              // L2 prefetch distance in stages
 
+// One work item of the pair engine. Gram items compute a 256 x 256 block (R, C), C >= R, of the
+// interleaved Gram matrix G = Y Y^T, in units of 256 Gram rows (128 inputs); fold items compute the
+// folded product D = S S^T - 2 A B^T of the 256-input super-block R = C (inputs 256 R .. 256 R + 255).
+struct PairItem {
+    int job, f, R, C;
+    bool dbl;    // fills both TMEM halves (a double or a twin)
+    bool twin;   // the last diagonal blocks of channels f and f + 1
+    bool wide;   // a single diagonal block in stages of 2 kKt samples
+    bool fold;   // a fold item (fold layout only)
+};
+
 // Work items of a frame-mode job: every 256x256 block (R, C >= R) of every channel its own item.
-// Work items of a packet-mode job, by pairs of channels (2c, 2c + 1), which share a packet group:
+// Work items of a packet-mode job with at most 128 inputs (one 256-row block per channel): its
+// diagonal block, by pairs of channels (2c, 2c + 1), which share a packet group:
 // - each channel's doubles: the diagonal block (R, R) together with its right neighbour (R, R + 1),
-//   R < S2 - 1, computed into the two TMEM halves from one operand stage (A = block R, B = block
-//   R + 1);
+//   R < S2 - 1, computed into the two TMEM halves from one operand stage (A = block R, B = block R
+//   + 1) (none at N <= 128);
 // - its singles (R, C >= R + 2);
 // - then one twin: the last diagonal block (S2 - 1, S2 - 1) of both channels, channel 2c's block in
 //   the A slot and channel 2c + 1's (N bytes further into the same packets) in the B slot, each
 //   multiplied by itself into its own TMEM half.
-// At N = 256 a channel pair is two doubles and a twin, all with 8 MMAs and four converted blocks
-// per stage: the items of neighbouring pairs run in lockstep and share their packets in L2. An odd
-// last channel ends with its diagonal block as a single (a wide one, 2 x kKt samples per stage).
-// Pairs take items pair, pair + pairs, ...; the launch uses an odd number of pairs. (Frame mode, with
-// 256-sample stages, runs every block as its own item: doubles make its stages MMA-bound, 0.80 ->
-// 0.84 ms.) dbl: the item fills both TMEM halves (a double or a twin); C = R + 1 for a double (the
-// block loaded as B), C = R for a twin.
-__device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C, bool &dbl,
-                                                 bool &twin) {
+// Integrations shorter than kTwinMinTime keep each channel's diagonal block as a wide single. Pairs
+// take items pair, pair + pairs, ... (Frame mode, with 256-sample stages, runs every block as its own
+// item: doubles make its stages MMA-bound, 0.80 -> 0.84 ms.)
+// Work items of a packet-mode job with more than 128 inputs (the fold layout), channel by channel:
+// - one fold item per whole 256-input super-block R: D = S S^T - 2 A B^T over its inputs, with
+//   s = a + b; the visibilities of the super-block are Re V = (D + D^T) / 2, Im V = (D - D^T) / 2, so
+//   its 2 x 2 Gram blocks (three of them on or above the diagonal) cost two block products;
+// - a half super-block at the end (N mod 256 in (0, 128]) as a Gram diagonal single;
+// - the Gram blocks between different super-blocks as singles (R, C) with R / 2 < C / 2.
+// Each fold item and single fills one TMEM half, so consecutive items alternate halves.
+__device__ __forceinline__ PairItem decode_pair_item(const Params &p, int g) {
+    PairItem it;
     int j = 0;
     while (j + 1 < p.n_jobs && g >= p.jobs[j + 1].item_begin) ++j;
     const Job &jb = p.jobs[j];
     int l = g - jb.item_begin;
-    job = j;
-    const int S2 = jb.nb;                     // 256-row super-blocks
-    twin = false;
-    dbl = false;
+    it.job = j;
+    it.dbl = it.twin = it.wide = it.fold = false;
+    const int S2 = jb.nb;                     // 256-row blocks (128 inputs each)
     int q;
-    if (!jb.twin) {
-        f = l / jb.strips;
+    if (jb.fold) {
+        it.f = l / jb.strips;
         q = l % jb.strips;
-        if (jb.doubles == 0) {                // frame mode: every block (R, C >= R) its own item
-            for (R = 0; R < S2; ++R) {
-                if (q < S2 - R) break;
-                q -= S2 - R;
+        const int n_fold = S2 / 2;
+        if (q < n_fold) {                     // fold item of super-block q
+            it.R = it.C = q;
+            it.fold = true;
+            return it;
+        }
+        q -= n_fold;
+        if (S2 & 1) {                         // the last half super-block's diagonal block
+            if (q == 0) {
+                it.R = it.C = S2 - 1;
+                return it;
             }
-            C = R + q;
-            return;
+            --q;
+        }
+        for (it.R = 0; it.R < S2; ++it.R) {   // blocks of different super-blocks
+            const int c0 = 2 * (it.R / 2 + 1), n = S2 - c0;
+            if (n > 0) {
+                if (q < n) {
+                    it.C = c0 + q;
+                    return it;
+                }
+                q -= n;
+            }
+        }
+        it.R = it.C = 0;                      // not reached
+        return it;
+    }
+    if (!jb.twin) {
+        it.f = l / jb.strips;
+        q = l % jb.strips;
+        if (jb.doubles == 0 && !p.wide_diag) {   // frame mode: every block (R, C >= R) its own item
+            for (it.R = 0; it.R < S2; ++it.R) {
+                if (q < S2 - it.R) break;
+                q -= S2 - it.R;
+            }
+            it.C = it.R + q;
+            return it;
         }
         if (q < jb.doubles) {                 // packet mode, channel by channel: doubles,
-            R = q;
-            C = R + 1;
-            dbl = true;
-            return;
+            it.R = q;
+            it.C = it.R + 1;
+            it.dbl = true;
+            return it;
         }
         q -= jb.doubles;                      // then singles, the last diagonal (wide) at the end
-        for (R = 0; R < S2 - 1; ++R) {
-            if (q < S2 - R - 2) break;
-            q -= S2 - R - 2;
+        for (it.R = 0; it.R < S2 - 1; ++it.R) {
+            if (q < S2 - it.R - 2) break;
+            q -= S2 - it.R - 2;
         }
-        C = R < S2 - 1 ? R + 2 + q : R;
-        return;
+        it.C = it.R < S2 - 1 ? it.R + 2 + q : it.R;
+        it.wide = p.wide_diag && it.R == it.C;
+        return it;
     }
     const int D = jb.doubles, per_ch = jb.doubles + jb.offdiag;
     const int per2 = jb.strips;               // 2 per_ch + 1 items per channel pair
@@ -726,51 +779,40 @@ __device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &jo
     q = l % per2;
     if (cp < jb.n_chan / 2) {
         if (q == per2 - 1) {                  // the twin of channels 2 cp and 2 cp + 1
-            f = 2 * cp;
-            R = C = S2 - 1;
-            dbl = twin = true;
-            return;
+            it.f = 2 * cp;
+            it.R = it.C = S2 - 1;
+            it.dbl = it.twin = true;
+            return it;
         }
-        f = 2 * cp + q / per_ch;              // q < 2 per_ch, so per_ch > 0 here
+        it.f = 2 * cp + q / per_ch;           // q < 2 per_ch, so per_ch > 0 here
         q %= per_ch;
     } else {                                  // the odd last channel: doubles, singles, its diagonal
-        f = jb.n_chan - 1;
+        it.f = jb.n_chan - 1;
         q = l - (jb.n_chan / 2) * per2;
     }
     if (q < D) {
-        R = q;
-        C = R + 1;
-        dbl = true;
-        return;
+        it.R = q;
+        it.C = it.R + 1;
+        it.dbl = true;
+        return it;
     }
     q -= D;
-    for (R = 0; R < S2 - 1; ++R) {
-        if (q < S2 - R - 2) break;
-        q -= S2 - R - 2;
+    for (it.R = 0; it.R < S2 - 1; ++it.R) {
+        if (q < S2 - it.R - 2) break;
+        q -= S2 - it.R - 2;
     }
-    C = R < S2 - 1 ? R + 2 + q : R;
+    it.C = it.R < S2 - 1 ? it.R + 2 + q : it.R;
+    it.wide = p.wide_diag && it.R == it.C;
+    return it;
 }
 
-__device__ __forceinline__ void decode_pair_item(const Params &p, int g, int &job, int &f, int &R, int &C) {
-    bool dbl, twin;
-    decode_pair_item(p, g, job, f, R, C, dbl, twin);
-}
-
-// Packet mode runs a single diagonal block (R, R) (an odd last channel's) in wide stages of 2 kKt
-// samples: samples
-// t0 .. t0 + kKt - 1 of block R in the A slot and t0 + kKt .. t0 + 2 kKt - 1 in the B slot, 8 MMAs
-// per stage with both operands from one slot. Its converters fill both slots as for a double, so
-// the per-stage cost (packet lookups, gather issue, hand-off) is paid once per 2 kKt samples.
-__device__ __forceinline__ bool item_wide(const Params &p, int R, int C, bool dbl) {
-    return p.wide_diag && R == C && !dbl;
-}
 // stages of an item and its drain interval in stages
 __device__ __forceinline__ void item_stages(const Params &p, const Job &jb, bool wide, int &k_tiles, int &flush) {
     k_tiles = wide ? jb.k_tiles_wide : jb.k_tiles;
     flush = wide ? p.k_flush_tiles_wide : p.k_flush_tiles;
 }
 
-// Walks the (item, k-tile) stages of one pair in order (forwarder and L2 prefetch).
+// Walks the (item, k-tile) stages of one pair in order (frame mode: forwarder and L2 prefetch).
 struct PairCursor {
     int g, kt, job, f, R, C, k_tiles;
     __device__ __forceinline__ void start(const Params &p, int g0) {
@@ -779,9 +821,12 @@ struct PairCursor {
         if (g < p.n_items) load(p);
     }
     __device__ __forceinline__ void load(const Params &p) {
-        bool dbl, twin;
-        decode_pair_item(p, g, job, f, R, C, dbl, twin);
-        k_tiles = item_wide(p, R, C, dbl) ? p.jobs[job].k_tiles_wide : p.jobs[job].k_tiles;
+        const PairItem it = decode_pair_item(p, g);
+        job = it.job;
+        f = it.f;
+        R = it.R;
+        C = it.C;
+        k_tiles = it.wide ? p.jobs[job].k_tiles_wide : p.jobs[job].k_tiles;
     }
     __device__ __forceinline__ bool valid(const Params &p) const { return g < p.n_items; }
     __device__ __forceinline__ void next(const Params &p, int n_pairs) {
@@ -797,7 +842,8 @@ constexpr uint32_t kNoPacket = 0xFFFFFFFFu;
 // One converter thread's walk over the stages of its pair. The thread converts inputs 16c ..
 // 16c + 15 of the A block and (unless the item is a plain diagonal single) of the B slot's block,
 // for samples t_row + r kRowStep (r < kRows) of each kKt-sample stage; a stage's address
-// arithmetic is two 64-bit adds.
+// arithmetic is two 64-bit adds. A fold item's two loads are inputs 16c .. and 64 + 16c .. of the
+// CTA's 128 inputs of the super-block (nblk = 3: they fill the S, A and B slots).
 // Frame mode: sample t of these bytes sits at frame + (t F + f) N + column.
 // Packet mode (the zero-copy path): sample t sits in packet o = owner[f / 8][t / 4] (the packet
 // holding time slot t / 4 of this channel's group), at pkts + o * pkt_stride + 16 + ((t % 4) 8 +
@@ -819,29 +865,38 @@ struct PairLoader {
     int64_t pstride;
 
     __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
-        int job, f, R, C;
-        bool dbl, twin;
-        decode_pair_item(p, g, job, f, R, C, dbl, twin);
-        const Job &jb = p.jobs[job];
+        const PairItem it = decode_pair_item(p, g);
+        const Job &jb = p.jobs[it.job];
         const int N = jb.n_inputs, F = jb.n_chan;
         kt = 0;
-        wide = kPackets && item_wide(p, R, C, dbl);
-        twin = kPackets && twin;
+        wide = kPackets && it.wide;
+        const bool twin = kPackets && it.twin;
         k_tiles = wide ? jb.k_tiles_wide : jb.k_tiles;
-        nblk = R == C && !wide && !twin ? 1 : 2;
+        int ca, cb;
+        if (kPackets && it.fold) {
+            // odd rows take the CTA's second 64 inputs first: their first stores then go to chunks
+            // 4..7 while even rows' go to chunks 0..3 (no shared-memory bank conflicts)
+            nblk = 3;
+            const int h = t_row & 1;
+            ca = 256 * it.R + 128 * (int)rank + 64 * h + 16 * c;
+            cb = 256 * it.R + 128 * (int)rank + 64 * (1 - h) + 16 * c;
+        } else {
+            nblk = it.R == it.C && !wide && !twin ? 1 : 2;
+            ca = (2 * it.R + (int)rank) * 64 + 16 * c;
+            cb = (2 * it.C + (int)rank) * 64 + 16 * c;
+        }
         t_left = jb.n_time - t_row;
-        const int ca = (2 * R + (int)rank) * 64 + 16 * c, cb = (2 * C + (int)rank) * 64 + 16 * c;
         va = ca < N;
-        vb = nblk == 2 && cb < N;
+        vb = nblk >= 2 && cb < N;
         const uint8_t *base;
         if constexpr (kPackets) {
             const int Q = jb.n_time / 4, lane = threadIdx.x & 31;
-            base = jb.pkts + 16 + ((size_t)(t_row & 3) * 8 + f % 8) * N;
-            own = jb.owner + (size_t)(f / 8) * Q + lane;
+            base = jb.pkts + 16 + ((size_t)(t_row & 3) * 8 + it.f % 8) * N;
+            own = jb.owner + (size_t)(it.f / 8) * Q + lane;
             s_left = Q - lane;
             pstride = jb.pkt_stride;
         } else {
-            base = jb.frame + ((size_t)t_row * F + f) * N;
+            base = jb.frame + ((size_t)t_row * F + it.f) * N;
             step = (int64_t)S::kKt * F * N;
             rstep = (int64_t)S::kRowStep * F * N;
         }
@@ -908,7 +963,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
     constexpr int kOpSlotBytes = kBlk * kKt;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int op_stage_bytes = kPairSlots * kOpSlotBytes;
+    const int op_stage_bytes = p.slots * kOpSlotBytes;
     uint8_t *op_ring = smem;
     uint64_t *bars = reinterpret_cast<uint64_t *>(op_ring + p.op_stages * op_stage_bytes);
     uint64_t *op_full = bars;                       // [op_stages] even CTA: both CTAs' converters
@@ -918,8 +973,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
     uint64_t *conv_done = acc_empty + 2;            // [op_stages] local: this CTA's converters finished
     uint64_t *epi_done = conv_done + p.op_stages;   // [2] local: this CTA's epilogue drained
     uint64_t *done = epi_done + 2;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *x_full = done + 1;                    // fold: the partner's epilogue filled this CTA's stage_x
+    uint64_t *x_empty = x_full + 1;                 // fold: the partner's epilogue finished reading its stage_x
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(x_empty + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    // fold epilogue staging (after the 1 KiB of barriers): stage_d = [32 rows][128 columns] of FP32
+    // accumulator values of this CTA's diagonal quadrant, stage_x = [32 rows][128 columns] received
+    // from the partner CTA; 16-byte chunks of a row are swizzled as chunk ^ (row & 7)
+    uint8_t *stage_d_ptr = op_ring + p.op_stages * op_stage_bytes + 1024;
+    const uint32_t stage_d = dev::smem_u32(stage_d_ptr);
+    const uint32_t stage_x = stage_d + kFoldStageD;
+    const float *stage_df = reinterpret_cast<const float *>(stage_d_ptr);
+    const float *stage_xf = reinterpret_cast<const float *>(stage_d_ptr + kFoldStageD);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = dev::cluster_ctarank();
@@ -940,6 +1005,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             dev::mbar_init(&epi_done[a], kPairEpiWarps);
         }
         dev::mbar_init(done, 1);
+        dev::mbar_init(x_full, 1);                  // CTA 1: the sending warp of CTA 0
+        dev::mbar_init(x_empty, kPairEpiWarps);     // CTA 0: the four epilogue warps of CTA 1
         *abort_flag = 0;
         dev::fence_mbar_init();
         if (!kPackets)
@@ -960,6 +1027,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         const uint64_t t0 = dev::globaltimer_ns();
         for (uint32_t it = 1;; ++it) {
             if (dev::mbar_try_wait(bar, parity)) return true;
+            if ((it & 127u) == 0) {
+                if (*abort_flag) return false;
+                if (dev::globaltimer_ns() - t0 > p.limit_ns) {
+                    *abort_flag = 1;
+                    atomicExch(p.status, XE_ETIMEOUT);
+                    return false;
+                }
+            }
+        }
+    };
+    // the same with cluster-scope acquire, for barriers guarding data the partner CTA wrote
+    auto wait_cluster = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if (dev::mbar_try_wait_cluster(bar, parity)) return true;
+        const uint64_t t0 = dev::globaltimer_ns();
+        for (uint32_t it = 1;; ++it) {
+            if (dev::mbar_try_wait_cluster(bar, parity)) return true;
             if ((it & 127u) == 0) {
                 if (*abort_flag) return false;
                 if (dev::globaltimer_ns() - t0 > p.limit_ns) {
@@ -1007,12 +1090,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             uint32_t acc = 0, acc_ph = 0;
             bool ok = true;
             for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-                int job, f, R, C;
-                bool dbl, twin;
-                decode_pair_item(p, g, job, f, R, C, dbl, twin);
-                dbl = kPackets && dbl;           // frame mode never runs doubles or twins
+                const PairItem it = decode_pair_item(p, g);
+                const bool dbl = kPackets && it.dbl;   // frame mode never runs doubles or twins
                 int kt_n, fl;
-                item_stages(p, p.jobs[job], kPackets && item_wide(p, R, C, dbl), kt_n, fl);
+                item_stages(p, p.jobs[it.job], kPackets && it.wide, kt_n, fl);
                 for (int k0 = 0; k0 < kt_n && ok; k0 += fl) {
                     for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {   // a double fills both halves
                         if (*abort_flag || !wait(&epi_done[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
@@ -1027,20 +1108,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         if (lane == 0 && leader) {
             // ---------------------------------------------------------------- pair MMA issuer (even CTA)
             constexpr uint32_t idesc = dev::idesc_e5m2_f32_mn(256, 256);
+            constexpr uint32_t idesc_s = dev::idesc_e4m3_f32_mn(256, 256);
             uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
             bool ok = true;
             for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-                int job, f, R, C;
-                bool dbl, twin;
-                decode_pair_item(p, g, job, f, R, C, dbl, twin);
-                dbl = kPackets && dbl;           // frame mode never runs doubles or twins
-                twin = kPackets && twin;
-                const Job &jb = p.jobs[job];
+                const PairItem it = decode_pair_item(p, g);
+                const bool dbl = kPackets && it.dbl;   // frame mode never runs doubles, twins or folds
+                const bool twin = kPackets && it.twin;
+                const bool fold = kPackets && it.fold;
+                const Job &jb = p.jobs[it.job];
                 // a single block multiplies A by B (B = A on the diagonal) into half acc; a double
                 // multiplies A by A into half acc and A by B into the other half; a twin A by A and B
-                // by B; a wide stage multiplies each slot by itself into half acc
-                const bool wide = kPackets && item_wide(p, R, C, dbl);
-                const uint32_t b_slot = R == C && !twin ? 0u : 1u;
+                // by B; a wide stage multiplies each slot by itself into half acc; a fold item adds
+                // S S^T (E4M3) and A B^T (E5M2; the A codes carry -2 a) into half acc
+                const bool wide = kPackets && it.wide;
+                const uint32_t b_slot = it.R == it.C && !twin ? 0u : 1u;
                 const uint32_t acc2 = acc ^ 1u;
                 int kt_n, fl;
                 item_stages(p, jb, wide, kt_n, fl);
@@ -1058,7 +1140,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                             const uint64_t ad = dev::sdesc_mn_sw128(sb + kk * 4096, kOpSlotBytes);
                             const uint64_t bd = dev::sdesc_mn_sw128(sb + b_slot * kOpSlotBytes + kk * 4096, kOpSlotBytes);
                             const uint32_t accum = (kt > k0 || kk > 0) ? 1u : 0u;
-                            if (dbl) {
+                            if (fold) {
+                                const uint64_t fa = dev::sdesc_mn_sw128(sb + kOpSlotBytes + kk * 4096, kOpSlotBytes);
+                                const uint64_t fb = dev::sdesc_mn_sw128(sb + 2 * kOpSlotBytes + kk * 4096, kOpSlotBytes);
+                                dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, ad, idesc_s, accum);
+                                dev::mma_f8f6f4_pair(tmem + acc * 256u, fa, fb, idesc, 1u);
+                            } else if (dbl) {
                                 dev::mma_f8f6f4_pair(tmem + acc * 256u, ad, ad, idesc, accum);
                                 dev::mma_f8f6f4_pair(tmem + acc2 * 256u, twin ? bd : ad, bd, idesc, accum);
                             } else if (wide) {
@@ -1090,32 +1177,195 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         // -------------------------------------------------------------------- epilogue (both CTAs)
         using O = Order<true>;
         constexpr int kPerQuarter = kPairEpiWarps / 4;
+        constexpr float kMagic = 12582912.0f;               // 1.5 * 2^23
+        constexpr int kMagicBits = 0x4B400000;
         const int q = warp & 3;
         const int half = (warp - kPairEpiWarp0) >> 2;
         const int m = q * 32 + lane;
         const bool im_row = O::comp_of(m) != 0;
-        uint32_t acc = 0, acc_ph = 0;
+        const uint32_t partner = rank ^ 1u;
+        uint32_t acc = 0, acc_ph = 0, x_ph = 0;
         bool ok = true;
-        for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-            int job, f, R, C_item;
-            bool dbl, twin;
-            decode_pair_item(p, g, job, f, R, C_item, dbl, twin);
-            dbl = kPackets && dbl;               // frame mode never runs doubles or twins
-            twin = kPackets && twin;
-            const Job &jb = p.jobs[job];
+        // Fold items synchronise the four epilogue warps with a named barrier, so every warp walks
+        // every item and leaves only together with the others: a warp that failed a wait skips the
+        // work of Gram items and says so at the next fold item's first barrier, where all decide.
+        for (int g = pair; g < p.n_items; g += n_pairs) {
+            const PairItem it = decode_pair_item(p, g);
+            if (!ok && !(kPackets && it.fold)) continue;
+            const bool dbl = kPackets && it.dbl;     // frame mode never runs doubles, twins or folds
+            const bool twin = kPackets && it.twin;
+            const Job &jb = p.jobs[it.job];
             const int N = jb.n_inputs;
-            const int rb = 2 * R + (int)rank;
+            int32_t *vis_f = jb.vis + (size_t)it.f * (size_t)npairs(N) * 2;
+            int kt_n, fl;
+            item_stages(p, jb, kPackets && it.wide, kt_n, fl);
+            if (kPackets && it.fold) {
+                // ------------------------------------------------------------ fold item
+                // This CTA holds rows 128 rank + m of D (scaled by 16) over the super-block's 256
+                // inputs, all 256 columns. V[i][j] (i <= j) needs D[i][j] and D[j][i]:
+                //   Re V = (D[i][j] + D[j][i]) / 32,  Im V = (D[i][j] - D[j][i]) / 32,
+                // formed in FP32 (both sums exact: |2 x 16 V| < 2^28 with at most 23 significant bits)
+                // and converted with the 1.5 * 2^23 trick (|V| <= 2^22 per drain segment). Every
+                // visibility is written by the thread holding row j of D (column by column: a warp
+                // writes 32 consecutive visibilities of one row), in four steps of 32 rows i: in step
+                // s, warp s stages its rows of this CTA's diagonal quadrant in stage_d (D[i][j] for the
+                // quadrant), and CTA 0's warp s sends its rows of the off-diagonal quadrant
+                // (D[i][128 .. 255]) into CTA 1's stage_x; CTA 1 writes that quadrant's V[i][j].
+                const int base = 256 * it.R;
+                const uint32_t tb = tmem + (uint32_t(q * 32) << 16);
+                auto prow_of = [N](int r) -> int32_t { return r * N - r * (r - 1) / 2 - r; };
+                // 16 visibilities (one half of a 32-column TMEM chunk): elem(c, pos, dij, dji) gives element
+                // c's position in the triangle, D[i][j] and D[j][i], and whether it is written. The old
+                // values (when adding) are all loaded first (sixteen loads in flight per thread) and through
+                // L2 only: cached in L1 they were an order of magnitude slower here.
+                auto chunk16 = [&](auto elem, bool add) {
+                    int2 o[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        int32_t pos;
+                        float a, b;
+                        const bool v = elem(c, pos, a, b);
+                        o[c] = add && v ? __ldcg(reinterpret_cast<const int2 *>(vis_f) + pos) : make_int2(0, 0);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        int32_t pos;
+                        float a, b;
+                        if (!elem(c, pos, a, b)) continue;
+                        const int re = __float_as_int(fmaf(a + b, 0.03125f, kMagic)) - kMagicBits;
+                        const int im = __float_as_int(fmaf(a - b, 0.03125f, kMagic)) - kMagicBits;
+                        __stcg(reinterpret_cast<int2 *>(vis_f) + pos, make_int2(re + o[c].x, im + o[c].y));
+                    }
+                };
+                // word offset of (row, col) in a [32][128] staging tile
+                auto off = [](int row, int col) -> int {
+                    return row * 128 + ((((col >> 2) ^ row) & 7) | ((col >> 2) & ~7)) * 4 + (col & 3);
+                };
+                const int j = base + 128 * (int)rank + m;            // this thread's row of D
+                if (jb.accumulate) {
+                    // the old values this item adds to go into L2 while its MMAs run: this warp writes
+                    // columns c0 .. c0 + 31 of rows base .. c0 + 31 (CTA 0: its quadrant; CTA 1: the
+                    // off-diagonal quadrant and its own), two 128-byte lines per row: lanes 0..15 take
+                    // the first line of every 16th row, lanes 16..31 the second
+                    const int c0 = base + 128 * (int)rank + 32 * q;
+                    const int r_end = min(c0 + 31, N - 1);
+                    if (c0 < N)
+                        for (int r = base + (lane & 15); r <= r_end; r += 16)
+                            dev::prefetch_l2(vis_f + 2 * (prow_of(r) + max(c0, r) + 16 * (lane >> 4)));
+                }
+                bool gone = false;
+                for (int k0 = 0; k0 < kt_n; k0 += fl) {
+                    const uint32_t ta = tb + acc * 256u;
+                    // (every decision that guards a warp-wide tcgen05.ld is made uniform across the warp)
+                    bool good = __all_sync(0xffffffffu, ok && !*abort_flag && wait(&acc_full[acc], (acc_ph >> acc) & 1u));
+                    if (!dev::named_sync_and(kEpiBar, 32 * kPairEpiWarps, good)) { gone = true; break; }
+                    dev::tc_fence_after();
+                    const bool add = jb.accumulate || k0 > 0;
+                    uint32_t d[32];
+                    uint32_t h16[16];
+                    const int qcol = 128 * (int)rank;                    // first TMEM column of the quadrant
+                    for (int st = 0; st < 4; ++st) {
+                        // the rows i = 32 st .. 32 st + 31 of this CTA (warp st's lanes)
+                        if (good && q == st) {
+                            if (rank == 0) {
+                                // D[i][128 .. 255] -> CTA 1's stage_x, once it has read the last rows
+                                good = __all_sync(0xffffffffu, wait_cluster(x_empty, x_ph ^ 1u));
+                                if (good) {
+                                    const uint32_t rx = dev::mapa(stage_x, 1);
+#pragma unroll 1
+                                    for (int k = 4; k < 8; ++k) {
+                                        dev::tmem_ld_32x32b_x32(ta + 32 * k, d);
+                                        dev::tmem_ld_wait();
+#pragma unroll
+                                        for (int c = 0; c < 32; c += 4)
+                                            dev::st_cluster_v4(rx + 4 * off(lane, 32 * (k - 4) + c), d[c], d[c + 1], d[c + 2], d[c + 3]);
+                                    }
+                                }
+                                asm volatile("fence.acq_rel.cluster;" ::: "memory");   // the stores above, then the arrival
+                                __syncwarp();
+                                if (lane == 0) dev::mbar_arrive_cluster(x_full, 1);
+                            }
+                            if (good) {                                  // the quadrant rows -> stage_d
+#pragma unroll 1
+                                for (int k = 0; k < 4; ++k) {
+                                    dev::tmem_ld_32x32b_x32(ta + qcol + 32 * k, d);
+                                    dev::tmem_ld_wait();
+#pragma unroll
+                                    for (int c = 0; c < 32; c += 4) {
+                                        const uint32_t a = stage_d + 4 * off(lane, 32 * k + c);
+                                        asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
+                                                     ::"r"(a), "r"(d[c]), "r"(d[c + 1]), "r"(d[c + 2]), "r"(d[c + 3]));
+                                    }
+                                }
+                            }
+                        }
+                        dev::named_sync(kEpiBar, 32 * kPairEpiWarps);
+                        if (good && q >= st) {
+                            // quadrant: V[i][j] for rows i = first + 32 st + r <= j; D[j][i] own (columns
+                            // 32 st .. of the quadrant), D[i][j] = stage_d[r][m]
+                            const bool j_ok = j < N;
+#pragma unroll 1
+                            for (int h = 0; h < 2; ++h) {
+                                dev::tmem_ld_32x32b_x16(ta + qcol + 32 * st + 16 * h, h16);
+                                dev::tmem_ld_wait();
+                                chunk16([&](int c, int32_t &pos, float &dij, float &dji) -> bool {
+                                    const int r = 16 * h + c, il = 32 * st + r, ii = base + 128 * (int)rank + il;
+                                    pos = prow_of(ii) + j;
+                                    dij = stage_df[off(r, m)];
+                                    dji = __uint_as_float(h16[c]);
+                                    return il <= m && j_ok;
+                                }, add);
+                            }
+                        }
+                        if (rank == 1) {
+                            // off-diagonal quadrant: V[i][j] for CTA 0's rows i = base + 32 st + r;
+                            // D[j][i] own (columns 32 st ..), D[i][j] = stage_x[r][m]
+                            good = __all_sync(0xffffffffu, good && wait_cluster(x_full, x_ph));
+                            if (good) {
+                                const bool j_ok = j < N;
+#pragma unroll 1
+                                for (int h = 0; h < 2; ++h) {
+                                    dev::tmem_ld_32x32b_x16(ta + 32 * st + 16 * h, h16);
+                                    dev::tmem_ld_wait();
+                                    chunk16([&](int c, int32_t &pos, float &dij, float &dji) -> bool {
+                                        const int r = 16 * h + c, ii = base + 32 * st + r;
+                                        pos = prow_of(ii) + j;
+                                        dij = stage_xf[off(r, m)];
+                                        dji = __uint_as_float(h16[c]);
+                                        return j_ok;
+                                    }, add);
+                                }
+                            }
+                            asm volatile("fence.acq_rel.cluster;" ::: "memory");   // the reads above, then the arrival
+                            __syncwarp();
+                            if (lane == 0) dev::mbar_arrive_cluster(x_empty, 0);
+                        }
+                        x_ph ^= 1u;
+                        dev::named_sync(kEpiBar, 32 * kPairEpiWarps);     // stage_d free for the next rows
+                    }
+                    dev::tc_fence_before();
+                    if (lane == 0) dev::mbar_arrive(&epi_done[acc]);
+                    acc_ph ^= 1u << acc;
+                    acc ^= 1u;
+                    if (!dev::named_sync_and(kEpiBar, 32 * kPairEpiWarps, good)) { gone = true; break; }
+                }
+                if (gone) {                           // every epilogue warp leaves here together
+                    *abort_flag = 1;
+                    break;
+                }
+                continue;
+            }
+            const int rb = 2 * it.R + (int)rank;
             const int i = rb * (kBlk / 2) + O::input_of(m);
             const bool i_ok = i < N;
             const int64_t prow = (int64_t)i * N - (int64_t)i * (i - 1) / 2 - i;
-            int32_t *vis_f = jb.vis + (size_t)f * (size_t)npairs(N) * 2;
             const int n_chunks = 2 * (kBlk / 32);
             if (kPackets && jb.accumulate && i_ok) {
                 // packet mode: the old values this item adds to go into L2 while its MMAs run (the
                 // drain of a half holds up the tensor core, a double item filling all of TMEM);
                 // frame mode measured slower with the prefetch
                 for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {
-                    const int jc = (2 * (dbl && !twin ? R + sub : C_item) * kBlk) / 2 + (im_row ? 8 : 0);
+                    const int jc = (2 * (dbl && !twin ? it.R + sub : it.C) * kBlk) / 2 + (im_row ? 8 : 0);
                     const int32_t *vis_s = vis_f + (twin ? (size_t)sub * (size_t)npairs(N) * 2 : 0);
 #pragma unroll 1
                     for (int ck = 0; ck < n_chunks; ++ck) {
@@ -1126,11 +1376,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                     }
                 }
             }
-            int kt_n, fl;
-            item_stages(p, jb, kPackets && item_wide(p, R, C_item, dbl), kt_n, fl);
             for (int k0 = 0; k0 < kt_n && ok; k0 += fl)
             for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {        // a double: block (R, R), then (R, R + 1)
-                const int C = dbl && !twin ? R + sub : C_item;      // a twin: (R, R) of channel f, then f + 1
+                const int C = dbl && !twin ? it.R + sub : it.C;    // a twin: (R, R) of channel f, then f + 1
                 const int cb0 = 2 * C;
                 int32_t *vis_s = vis_f + (twin ? (size_t)sub * (size_t)npairs(N) * 2 : 0);
                 if (*abort_flag || !wait(&acc_full[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
@@ -1177,25 +1425,37 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         // -------------------------------------------------------------------- converters (both CTAs)
         // thread ctid converts inputs 16c .. 16c + 15 of samples t_row + r kRowStep (t_row = ctid / 4)
         // of each block: 16 packed bytes in, 32 E5M2 codes out into the two 16-byte chunks 2c and
-        // 2c + 1 of those operand rows (128-byte swizzle; all of a thread's rows share its phase)
+        // 2c + 1 of those operand rows (128-byte swizzle; all of a thread's rows share its phase). A
+        // fold item's two loads give 16 codes each for the S, A and B slots, at chunks c and 4 + c
+        // (odd rows: 4 + c first).
         const int ctid = threadIdx.x - 32 * kPairConvWarp0;
         const int t_row = ctid >> 2, c = ctid & 3;
         const uint32_t dst0 = t_row * 128 + (((2 * c) ^ (t_row & 7)) << 4);
         const uint32_t dst1 = t_row * 128 + (((2 * c + 1) ^ (t_row & 7)) << 4);
+        const uint32_t dsta = t_row * 128 + (((4 * (t_row & 1) + c) ^ (t_row & 7)) << 4);
+        const uint32_t dstb = t_row * 128 + (((4 * (1 - (t_row & 1)) + c) ^ (t_row & 7)) << 4);
         constexpr uint32_t kRowBytes = S::kRowStep * 128;
+        auto st16 = [](uint32_t a, const uint4 &v) {
+            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w));
+        };
         auto convert = [&](uint32_t slot, const uint4 &v) {
             uint4 lo, hi;
             dev::expand16_e5m2(v, lo, hi);
-            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
-                         ::"r"(slot + dst0), "r"(lo.x), "r"(lo.y), "r"(lo.z), "r"(lo.w));
-            asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
-                         ::"r"(slot + dst1), "r"(hi.x), "r"(hi.y), "r"(hi.z), "r"(hi.w));
+            st16(slot + dst0, lo);
+            st16(slot + dst1, hi);
+        };
+        auto convert_fold = [&](uint32_t row, uint32_t dst, const uint4 &v) {
+            uint4 fs, fa, fb;
+            dev::fold16(v, fs, fa, fb);
+            st16(row + dst, fs);
+            st16(row + kOpSlotBytes + dst, fa);
+            st16(row + 2 * kOpSlotBytes + dst, fb);
         };
         constexpr int kOwn = PairLoader<kPackets>::kOwnMax;
         struct Buf {
             uint4 a[S::kRows], b[S::kRows];
             uint32_t own[kOwn];                       // packets of the stage this buffer receives next
-            int nb;                                   // blocks of the stage it holds (0: none)
+            int nb;                                   // blocks of the stage it holds (0: none; 3: fold)
         };
         // samples of kBufs - 1 stages ahead are in flight while a stage is converted: kBufs buffers
         // in rotation (the loop is unrolled so that no buffer is copied); packet mode looks up a
@@ -1255,11 +1515,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             for (int q = 0; q < kOwn; ++q) lb.own[q] = nown[q];
             if (!wait(&op_empty[os], oph ^ 1)) return false;
             const uint32_t op = op_base + os * op_stage_bytes;
+            if (kPackets && cb.nb == 3) {
 #pragma unroll
-            for (int r = 0; r < S::kRows; ++r) convert(op + r * kRowBytes, cb.a[r]);
-            if (cb.nb == 2) {
+                for (int r = 0; r < S::kRows; ++r) {
+                    convert_fold(op + r * kRowBytes, dsta, cb.a[r]);
+                    convert_fold(op + r * kRowBytes, dstb, cb.b[r]);
+                }
+            } else {
 #pragma unroll
-                for (int r = 0; r < S::kRows; ++r) convert(op + kOpSlotBytes + r * kRowBytes, cb.b[r]);
+                for (int r = 0; r < S::kRows; ++r) convert(op + r * kRowBytes, cb.a[r]);
+                if (cb.nb == 2) {
+#pragma unroll
+                    for (int r = 0; r < S::kRows; ++r) convert(op + kOpSlotBytes + r * kRowBytes, cb.b[r]);
+                }
             }
             dev::fence_proxy_async_smem();            // operand visible to the tensor core
             __syncwarp();
@@ -1421,7 +1689,7 @@ static int launch_gemm(const Params &hp, int ctas, int smem, cudaStream_t st) {
 // Pair engine: as many 2-CTA clusters as can be resident at once (each CTA fills an SM), one per
 // work item at most.
 template <bool kPackets>
-static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaStream_t st) {
+static int launch_pair(const Params &hp, int items, int n_ctas, int smem, bool odd_pairs, cudaStream_t st) {
     static int max_pairs[64] = {};
     int dev = 0;
     XE_TRY_CUDA(cudaGetDevice(&dev));
@@ -1446,9 +1714,9 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, cudaSt
     }
     int pairs = std::min(items, max_pairs[dev]);
     if (n_ctas > 0) pairs = std::max(1, std::min(pairs, n_ctas / 2));
-    // packet mode interleaves doubles and singles channel by channel: an odd pair count makes every
-    // pair alternate between the two kinds
-    if (kPackets && pairs > 1 && pairs % 2 == 0) --pairs;
+    // the packet-mode Gram layout interleaves doubles and singles channel by channel: an odd pair
+    // count makes every pair alternate between the two kinds (fold items are all alike)
+    if (odd_pairs && pairs > 1 && pairs % 2 == 0) --pairs;
     correlate_pair_kernel<kPackets><<<2 * pairs, PairShape<kPackets>::kThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
@@ -1539,7 +1807,19 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         int64_t job_items = 0;
         if (engine == kFusedPair) {             // 256x256 blocks on or above the diagonal
             d.nb = (g.nb + 1) / 2;
-            if (pk) {
+            d.fold = 0;
+            if (pk && d.nb >= 2) {
+                // fold layout: per channel S2 / 2 fold items, a Gram diagonal single for an odd last
+                // block, and the Gram blocks (R, C) between different super-blocks (R / 2 < C / 2)
+                d.fold = 1;
+                d.doubles = 0;
+                d.offdiag = 0;
+                d.twin = 0;
+                int per_ch = d.nb / 2 + (d.nb & 1);
+                for (int r = 0; r < d.nb; ++r) per_ch += std::max(0, d.nb - 2 * (r / 2 + 1));
+                d.strips = per_ch;
+                job_items = (int64_t)d.strips * s.n_chan;
+            } else if (pk) {
                 // per channel S2 - 1 doubles and (S2 - 1)(S2 - 2) / 2 singles; then long
                 // integrations take the last diagonal blocks of channel pairs as twins (an odd last
                 // channel keeps its diagonal single), short ones each channel's as a wide single
@@ -1593,11 +1873,23 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     const int bar_bytes = 1024;
     const int avail = kSmemMax - 1024 - bar_bytes;
     const int op_slot = kBlk * kt_of(engine, pk != nullptr), pk_slot = 64 * kt_of(engine);
+    int staging = 0;
+    bool all_fold = nj > 0;
+    for (int j = 0; j < nj; ++j) {
+        hp.fold |= hp.jobs[j].fold;
+        all_fold = all_fold && hp.jobs[j].fold;
+    }
     if (engine == kFusedPair) {
-        hp.slots = kPairSlots;
+        // fold items need three operand slots per stage and the epilogue's transpose staging. The
+        // ring is as deep as fits in kPairSmemBudget: beyond it the SM takes its largest
+        // shared-memory carve-out, and the L1 left over (28 instead of 60 KB) no longer holds the
+        // converters' samples in flight (~48 KB per SM): measured 5.9 against 4.3 ms per
+        // full-band 8-frame call with the same four stages (fold layout)
+        hp.slots = hp.fold ? kFoldSlots : kPairSlots;
+        staging = hp.fold ? kFoldStageBytes : 0;
         hp.n_acc = 2;
         hp.pk_stages = 0;
-        hp.op_stages = std::min(kPairMaxStages, avail / (hp.slots * op_slot));
+        hp.op_stages = std::min(kPairMaxStages, (kPairSmemBudget - 1024 - bar_bytes - staging) / (hp.slots * op_slot));
     } else if (engine == kFusedMN) {
         hp.pk_stages = 3;
         hp.op_stages = std::min(8, (avail - hp.pk_stages * hp.slots * pk_slot) / (hp.slots * op_slot));
@@ -1606,10 +1898,11 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         hp.op_stages = std::min(8, avail / (hp.slots * op_slot));
     }
     if (hp.op_stages < 2) return XE_EINVAL;
-    const int smem = 1024 + hp.op_stages * hp.slots * op_slot + hp.pk_stages * hp.slots * pk_slot + bar_bytes;
+    const int smem = 1024 + hp.op_stages * hp.slots * op_slot + hp.pk_stages * hp.slots * pk_slot + bar_bytes + staging;
     XE_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
     if (engine == kFusedPair)
-        return pk ? launch_pair<true>(hp, items, tune.n_ctas, smem, st) : launch_pair<false>(hp, items, tune.n_ctas, smem, st);
+        return pk ? launch_pair<true>(hp, items, tune.n_ctas, smem, !all_fold, st)
+                  : launch_pair<false>(hp, items, tune.n_ctas, smem, false, st);
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     switch (engine) {
         case kUnpackedK: return launch_gemm<kUnpackedK>(hp, ctas, smem, st);

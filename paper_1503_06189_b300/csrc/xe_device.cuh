@@ -94,6 +94,21 @@ __device__ __forceinline__ void named_sync(uint32_t id, uint32_t nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// Named barrier that also ANDs a predicate over its `nthreads` participants: every thread gets the
+// same result, so a group of warps can take a decision together.
+__device__ __forceinline__ bool named_sync_and(uint32_t id, uint32_t nthreads, bool pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.and.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred ? 1u : 0u), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 // try_wait with cluster-scope acquire (for barriers other CTAs of the cluster arrive on).
 __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t parity) {
     uint32_t done;
@@ -105,6 +120,22 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t *bar, uint32_t pa
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return done != 0;
+}
+
+// Address of the shared-memory location `saddr` (a shared::cta address) in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(saddr), "r"(rank));
+    return remote;
+}
+
+// Stores into another CTA's shared memory (a shared::cluster address from mapa).
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
 }
 
 // ------------------------------------------------------------------ proxies / TMA
@@ -258,6 +289,16 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&r)
         : "r"(taddr)
         : "memory");
 }
+// 32 lanes x 16 consecutive 32-bit TMEM columns -> 16 registers per thread (thread = lane).
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -279,6 +320,11 @@ __device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t lbo)
 // Same as idesc_e5m2_f32 with both operands MN-major (transpose bits 15 and 16 set).
 __host__ __device__ constexpr uint32_t idesc_e5m2_f32_mn(uint32_t m, uint32_t n) {
     return idesc_e5m2_f32(m, n) | (1u << 15) | (1u << 16);
+}
+
+// Same as idesc_e5m2_f32_mn with E4M3 x E4M3 operands (format code 0 in both type fields).
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32_mn(uint32_t m, uint32_t n) {
+    return (1u << 4) | ((n >> 3) << 17) | ((m >> 4) << 24) | (1u << 15) | (1u << 16);
 }
 
 // ------------------------------------------------------------------ 4-bit -> E5M2
@@ -332,6 +378,52 @@ __device__ __forceinline__ void expand16_e5m2(const uint4 &in, uint4 &lo, uint4 
     expand4_e5m2(in.y, lo.z, lo.w);
     expand4_e5m2(in.z, hi.x, hi.y);
     expand4_e5m2(in.w, hi.z, hi.w);
+}
+
+// Operands of the folded product D = S S^T - 2 A B^T (a = Re x, b = Im x, s = a + b), scaled so that
+// D carries a factor 16: four packed samples (bytes re<<4 | im) -> ws = E4M3 codes of 4s, wa = E5M2
+// codes of -8a, wb = E5M2 codes of 4b (one code per sample, samples 0..3 in bytes 0..3); then
+// S S^T = 16 s s and A B^T = -32 a b.
+// Per half-precision lane: (x & 0x00F0) ^ 0x6080 has the bits of 512 + 8 (a ^ 8) = 576 + 8a, and
+// (x & 0x000F) ^ 0x6C08 those of 4096 + 4 (b ^ 8) = 4128 + 4b; 576 - (.) and (.) - 4128 are exact
+// and leave -8a and 4b, whose at most three significant bits sit in the high byte of the half: that
+// byte is the E5M2 code. -0.5 (-8a) + 4b = 4s is exact too; |4s| <= 64 with at most four
+// significant bits, so its E4M3 conversion is exact.
+__device__ __forceinline__ void fold4(uint32_t x, uint32_t &ws, uint32_t &wa, uint32_t &wb) {
+    uint32_t x8, re02, re13, im02, im13;
+    asm("shr.b32 %0, %1, 8;" : "=r"(x8) : "r"(x));
+    // lut 0x6A: (a & b) ^ c
+    asm("lop3.b32 %0, %1, 0x00F000F0, 0x60806080, 0x6A;" : "=r"(re02) : "r"(x));
+    asm("lop3.b32 %0, %1, 0x00F000F0, 0x60806080, 0x6A;" : "=r"(re13) : "r"(x8));
+    asm("lop3.b32 %0, %1, 0x000F000F, 0x6C086C08, 0x6A;" : "=r"(im02) : "r"(x));
+    asm("lop3.b32 %0, %1, 0x000F000F, 0x6C086C08, 0x6A;" : "=r"(im13) : "r"(x8));
+    // 576, 4128, -0.5 as half pairs
+    const uint32_t k_re = 0x60806080u, k_im = 0x6C086C08u, k_half = 0xB800B800u;
+    uint32_t na02, na13, b02, b13, s02, s13;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(na02) : "r"(k_re), "r"(re02));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(na13) : "r"(k_re), "r"(re13));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(b02) : "r"(im02), "r"(k_im));
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(b13) : "r"(im13), "r"(k_im));
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(s02) : "r"(na02), "r"(k_half), "r"(b02));
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(s13) : "r"(na13), "r"(k_half), "r"(b13));
+    wa = __byte_perm(na02, na13, 0x7351);
+    wb = __byte_perm(b02, b13, 0x7351);
+    // E4M3 pairs (samples 0, 2) and (1, 3), each half's code in the byte of the same position
+    uint32_t c;
+    asm("{\n\t.reg .b16 l, h;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f16x2 l, %1;\n\t"
+        "cvt.rn.satfinite.e4m3x2.f16x2 h, %2;\n\t"
+        "mov.b32 %0, {l, h};\n\t}"
+        : "=r"(c) : "r"(s02), "r"(s13));
+    ws = __byte_perm(c, 0, 0x3120);
+}
+
+// 16 packed samples -> 16 codes each of 4s (E4M3), -8a and 4b (E5M2), in input order.
+__device__ __forceinline__ void fold16(const uint4 &in, uint4 &s, uint4 &a, uint4 &b) {
+    fold4(in.x, s.x, a.x, b.x);
+    fold4(in.y, s.y, a.y, b.y);
+    fold4(in.z, s.z, a.z, b.z);
+    fold4(in.w, s.w, a.w, b.w);
 }
 
 }  // namespace dev

@@ -51,3 +51,28 @@ def e5m2_codes(frame):
     out[:, :T, row_re] = code(16 * re).transpose(1, 0, 2)
     out[:, :T, row_re + 4] = code(im).transpose(1, 0, 2)
     return out, R, ldy
+
+
+_CUDART = None
+
+
+def d2h(ptr, nbytes, dtype):
+    """Copy nbytes at a raw device address (a pointer libxe returned) into a numpy array of dtype."""
+    import ctypes
+
+    global _CUDART
+    if _CUDART is None:
+        torch.zeros(1, device="cuda")                   # the runtime and its context exist
+        for name in ("libcudart.so.13", "libcudart.so"):
+            try:
+                L = ctypes.CDLL(name)
+            except OSError:
+                continue
+            L.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+            _CUDART = L
+            break
+        if _CUDART is None:
+            raise RuntimeError("no CUDA runtime library")
+    out = np.empty(nbytes, np.uint8)
+    assert _CUDART.cudaMemcpy(out.ctypes.data, ptr, nbytes, 2) == 0     # device to host
+    return out.view(dtype)
