@@ -13,11 +13,12 @@ Prints one JSON line (rank 0). Metric: CMAC/s (complex multiply-accumulates of t
 visibilities, F * N(N+1)/2 * T per frame) and the real-time factor.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl xe|reference] [--frames 64]
-    python bench.py --config 1|2|4 [--impl xe|reference]   # the other workloads, frames in HBM
+    python bench.py --config 1|2|4|6 [--impl xe|reference]   # the other workloads, frames in HBM
 
 --config 1: N=16, F=4, T=4096 uniform nibbles; 2: the per-server Pathfinder frame N=256, F=64,
 T=16384 (signal model); 4: 24 uneven jobs (N 64..2048, F 16..256, T 1024..32768) in one batched
-launch. For these the step is correlation + normalisation of frames already in HBM.
+launch; 6: the full-CHIME scale per server, N=2048, F=64, T=16384. For these the step is
+correlation + normalisation of frames already in HBM.
 """
 from __future__ import annotations
 
@@ -208,7 +209,8 @@ def link_gbs(torch, dev, nbytes: int = 1 << 30) -> float:
     return best
 
 
-def run_serving(xe, torch, dev, pk, offered_gbps, feed: str = "host", seed: int = 5000, ring_frames: int = 6):
+def run_serving(xe, torch, dev, pk, offered_gbps, feed: str = "host", seed: int = 5000, ring_frames: int = 6,
+                frames_per_stream: int = 8):
     """Configuration 5 through xe_stream_*: the 8 streams' packets arrive as Poisson processes
     totalling `offered_gbps` of payload (None: as fast as the producer loop submits them), from
     pinned host memory (feed "host": H2D copies) or from device memory (feed "device": D2D copies,
@@ -222,7 +224,6 @@ def run_serving(xe, torch, dev, pk, offered_gbps, feed: str = "host", seed: int 
     host, devp, hdrs = pk
     S, GPS, N, T = 8, 16, 256, 4096
     stride = synth.packet_stride(N)
-    frames_per_stream = host[0].shape[0] // (T // 4 * GPS)
     rng = np.random.default_rng(seed)
     if offered_gbps:
         rate = offered_gbps * 1e9 / 8 / synth.payload_bytes(N) / S         # packets/s per stream
@@ -405,6 +406,17 @@ def run_xe(args):
             xe.xe_normalize(vis, xe.Shape(N, F, FR * T), FR * T, lost, out, stream=stream)
         return step, len(cl)
 
+    # the autotuner picks the pair engine's layout and launch shape for the calls this run makes
+    from paper_1503_06189_b300 import autotune
+    table = autotune.Table(None)
+    table.tune_packets(N, G * T)
+    if G > 1:
+        table.tune_packets(N, T)
+    table.install()
+    tuning = [{k: e[k] for k in ("n_inputs", "t_bucket", "mode", "layout", "pairs", "odd_pairs", "k_flush", "ms")}
+              for e in table.entries.values()]
+    print(f"[bench] tuning {tuning}", file=sys.stderr, flush=True)
+
     step, n_calls = make_step(G)
     launches_per_step = n_calls * 4 + 1           # per call: init, claim, tally, correlation; + normalise
 
@@ -512,6 +524,7 @@ def run_xe(args):
                                "CTA-pair tcgen05 correlation), 8 int ops per CMAC, timed by CUDA events around each call",
                      "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
         "gpu_launches": launches_per_step * args.steps,
+        "tuning": tuning,
         "graph_ms_per_step": graph_ms,
         "one_call_per_frame": per_frame,
         "engine_baselines": baselines,
@@ -684,6 +697,8 @@ def config_shapes(cfg):
         return [(16, 4, 4096)]
     if cfg == 2:
         return [(256, 64, 16384)]
+    if cfg == 6:
+        return [(2048, 64, 16384)]
     import synth
     return synth.config4_shapes()
 
@@ -693,14 +708,16 @@ def config_workload(cfg):
             2: "Pathfinder per-server frame: N=256, F=64, T=16384 (256 MiB), signal model (seed 2); "
                "correlate + normalise",
             4: "uneven batch: 24 jobs (seed 4), N 64..2048, F 16..256, T 1024..32768 (27.6 GiB of frames), "
-               "one batched correlation launch + per-job normalise"}[cfg]
+               "one batched correlation launch + per-job normalise",
+            6: "full-CHIME scale per server: N=2048, F=64, T=16384 (2 GiB), signal model (seed 6); "
+               "correlate + normalise"}[cfg]
 
 
 def config_frame_host(cfg, k, N, F, T):
     import synth
     if cfg == 1:
         return synth.uniform_frame(N, F, T, 1)
-    return synth.signal_frame(N, F, T, 2 if cfg == 2 else 4000 + k)
+    return synth.signal_frame(N, F, T, {2: 2, 6: 6}.get(cfg, 4000 + k))
 
 
 def run_config_reference(args):
@@ -714,7 +731,7 @@ def run_config_reference(args):
     order = sorted(range(len(shapes)), key=lambda k: shapes[k][0] ** 2 * shapes[k][2])
     for k in order:
         N, F, T = shapes[k]
-        chans = F if cfg != 4 else 1
+        chans = F if cfg in (1, 2) else 1
         fr = config_frame_host(cfg, k, N, chans, T)
         reps = 0
         while reps == 0 or (cfg == 1 and dt < 2.0):        # the tiny frame: repeat for ~2 s
@@ -729,8 +746,19 @@ def run_config_reference(args):
         if cfg != 4 or dt >= 10.0:
             break
     return {"value": cmac / dt, "unit": "CMAC/s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": ("full configuration: " if cfg != 4 else "bounded sample: ") + "; ".join(done)
+            "sample": ("full configuration: " if cfg in (1, 2) else "bounded sample: ") + "; ".join(done)
                       + f" ({dt:.1f} s of CPU work)", "seconds": dt}
+
+
+def useful_mma_fraction(shapes):
+    """Useful real MACs (4 per CMAC) over the MMA work the frame-mode pair engine issues (whole
+    256 x 256 blocks of the 2N-row Gram matrix on or above the block diagonal)."""
+    useful = issued = 0
+    for N, F, T in shapes:
+        nb = -(-2 * N // 256)
+        useful += 4 * npairs(N) * F * T
+        issued += nb * (nb + 1) // 2 * 256 * 256 * F * T
+    return useful / issued
 
 
 def run_config(args):
@@ -750,7 +778,7 @@ def run_config(args):
         if cfg == 1:
             fr = torch.from_numpy(config_frame_host(cfg, k, N, F, T)).to(dev)
         else:
-            fr = synth.signal_frame_torch(N, F, T, 2 if cfg == 2 else 4000 + k, device=dev,
+            fr = synth.signal_frame_torch(N, F, T, {2: 2, 6: 6}.get(cfg, 4000 + k), device=dev,
                                           chunk=max(1, (1 << 27) // (T * N)))
         frames.append(fr)
         vis.append(torch.empty((F, npairs(N), 2), dtype=torch.int32, device=dev))
@@ -759,7 +787,17 @@ def run_config(args):
     jobs = [(fr, v, xe.Shape(*sh), False) for fr, v, sh in zip(frames, vis, shapes)]
     ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    reps = {1: 2000, 2: 20, 4: 1}[cfg]                 # launches per step: a step lasts >= ~10 ms
+    # configuration 4: the autotuner picks the pair engine's launch shape per (N, T-bucket) of the jobs
+    tuning = None
+    if cfg == 4:
+        from paper_1503_06189_b300 import autotune
+        table = autotune.Table(None)
+        for N, F, T in shapes:
+            table.tune_frames(N, T)
+        table.install()
+        tuning = [{k: e[k] for k in ("n_inputs", "t_bucket", "mode", "pairs", "odd_pairs", "ms")}
+                  for e in table.entries.values()]
+    reps = {1: 2000, 2: 20, 4: 1, 6: 2}[cfg]           # launches per step: a step lasts >= ~10 ms
     cmac_step = reps * sum(F * npairs(N) * T for N, F, T in shapes)
     n_ev = reps * max(args.steps, 1)
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_ev)]
@@ -795,6 +833,30 @@ def run_config(args):
     corr_ms = statistics.mean(a.elapsed_time(b) for a, b in zip(ev0, ev1))
     clocks = clk.summary()
 
+    # the same step captured once into a CUDA graph and replayed
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            step()
+        with torch.cuda.stream(stream):
+            g.replay()
+        torch.cuda.synchronize(dev)
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gms = 0.0
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 0xFF)
+                r0.record(stream)
+                g.replay()
+                r1.record(stream)
+            torch.cuda.synchronize(dev)
+            gms += r0.elapsed_time(r1)
+        graph_ms = gms / args.steps
+        del g
+    except Exception as exc:
+        print(f"[bench] graph capture failed: {exc}", file=sys.stderr)
+
     # end to end: frames from pinned host memory, correlate + normalise, results back
     e2e = None
     try:
@@ -822,7 +884,7 @@ def run_config(args):
     pk, how = peaks()
     peak_tflops = 2.0 * pk["bf16_tflops_sustained"]
     achieved = cmac_step / reps * 8 / (corr_ms / 1e3) / 1e12
-    sky = {1: 4096, 2: 16384}.get(cfg)
+    sky = {1: 4096, 2: 16384, 6: 16384}.get(cfg)
     line = {
         "metric": METRIC, "value": cmac_step / (ms / 1e3), "unit": "CMAC/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -831,11 +893,17 @@ def run_config(args):
                    "l2": "256 MiB written between steps" + ("; the tiny frame itself fits in L2" if cfg == 1 else "")},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
+                     "useful_mma_fraction": useful_mma_fraction(shapes),
                      "kernel": "xe_correlate_batched (CTA-pair tcgen05 correlation), 8 int ops per CMAC",
                      "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
         "gpu_launches": args.steps * reps * (1 + len(shapes)),
         "clocks": clocks, "e2e": e2e,
     }
+    if cfg == 4:
+        line["tuning"] = tuning
+        line["graph_ms_per_step"] = graph_ms
+    else:
+        line["graph_ms_per_step"] = graph_ms
     if sky:
         line["realtime_factor"] = cmac_step / (ms / 1e3) / (npairs(shapes[0][0]) * shapes[0][1] * SAMPLE_RATE)
     base = run_config_reference(args)
@@ -855,8 +923,8 @@ def main():
                          "stays in tensor memory across them)")
     ap.add_argument("--impl", choices=["xe", "reference"], default="xe")
     ap.add_argument("--no-serving", action="store_true", help="skip the configuration-5 serving run")
-    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4], default=3,
-                    help="3: the full-band integration (default); 1, 2, 4: the other workloads")
+    ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 6], default=3,
+                    help="3: the full-band integration (default); 1, 2, 4: the other workloads; 6: N=2048 per server")
     args = ap.parse_args()
     if args.impl == "reference":
         if args.config != 3:

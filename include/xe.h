@@ -184,6 +184,46 @@ int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate,
  */
 int xe_probe_mma_legacy(int32_t kind, int32_t blocks, int32_t iters, int32_t *sink, void *stream);
 
+/* ---------------------------------------------------------------- tuning table (A6) */
+
+/* Item layouts of the CTA-pair engine in packet mode (xe_correlate_packets, the serving loop). */
+#define XE_LAYOUT_AUTO 0       /* fold for N > 128; below, Gram blocks with twins from T >= 16384 */
+#define XE_LAYOUT_GRAM 1       /* Gram blocks: doubles and singles, twins from T >= 16384, wide singles below */
+#define XE_LAYOUT_GRAM_TWIN 2  /* Gram blocks, twins at any T */
+#define XE_LAYOUT_GRAM_WIDE 3  /* Gram blocks, wide singles at any T */
+#define XE_LAYOUT_FOLD 4       /* one fold item per whole 256-input super-block (N > 128; else GRAM) */
+
+/*
+ * One entry of the library's tuning table: the choices of the CTA-pair engine for jobs with N inputs
+ * and t_bucket / 2 < T <= t_bucket (t_bucket a power of two >= 128) in one mode (packets or
+ * frames). The table is filled by an
+ * autotuner that measures the candidates on the device (paper_1503_06189_b300/autotune.py) and is
+ * consulted by every pair-engine launch: a batched launch takes each job's layout from its own
+ * entry, and the launch-wide choices (pairs, odd_pairs, k_flush) from the entry of its largest job.
+ * A non-zero field of an explicit xe_tune argument overrides the table.
+ */
+#define XE_TUNE_PACKETS 0      /* entry for packet-mode launches (xe_correlate_packets, serving loop) */
+#define XE_TUNE_FRAMES 1       /* entry for frame-mode launches (xe_correlate, xe_correlate_batched) */
+
+typedef struct {
+    int32_t n_inputs;   /* N of the entry */
+    int32_t t_bucket;   /* T bucket: power of two >= 128 */
+    int32_t mode;       /* XE_TUNE_PACKETS or XE_TUNE_FRAMES */
+    int32_t layout;     /* XE_LAYOUT_* (packet mode; frame mode: XE_LAYOUT_AUTO) */
+    int32_t pairs;      /* CTA pairs per launch, 0 = as many as can be resident */
+    int32_t odd_pairs;  /* 1: an odd pair count, 0: as counted, -1: the layout's default (odd for Gram) */
+    int32_t k_flush;    /* drain interval in samples, multiple of 128 up to 32768; 0 = default */
+} xe_tune_entry;
+
+#define XE_TUNE_MAX_ENTRIES 256
+
+/* Replaces the tuning table (n = 0 clears it; then every job takes the built-in choices).
+ * Host memory, read during the call. Errors: XE_EINVAL (n < 0 or > XE_TUNE_MAX_ENTRIES, an entry
+ * with a field out of range, or two entries for one (N, t_bucket)). */
+int xe_tune_table_set(const xe_tune_entry *entries, int32_t n);
+/* Copies up to cap entries of the table into out (host memory); returns the number of entries. */
+int xe_tune_table_get(xe_tune_entry *out, int32_t cap);
+
 /* ---------------------------------------------------------------- A6: batched persistent */
 
 #define XE_MAX_JOBS 64

@@ -21,11 +21,15 @@ XE_MAX_TIME = (1 << 24) - 1
 XE_MAX_JOBS = 64
 XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K, XE_ENGINE_FUSED_PAIR = 0, 1, 2, 3, 4
 XE_ENGINE_LEGACY_S4, XE_ENGINE_LEGACY_S8 = 5, 6
+XE_LAYOUT_AUTO, XE_LAYOUT_GRAM, XE_LAYOUT_GRAM_TWIN, XE_LAYOUT_GRAM_WIDE, XE_LAYOUT_FOLD = 0, 1, 2, 3, 4
+XE_TUNE_MAX_ENTRIES = 256
+XE_TUNE_PACKETS, XE_TUNE_FRAMES = 0, 1
 
 EXPORTED = [
     "xe_strerror", "xe_last_cuda_error", "xe_version", "xe_device_status", "xe_selftest_timeout",
     "xe_assemble_workspace_size", "xe_assemble", "xe_assemble_noalloc", "xe_unpack", "xe_correlate_workspace_size",
-    "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched",
+    "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched", "xe_tune_table_set",
+    "xe_tune_table_get",
     "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_flag_counts_workspace_size",
     "xe_flag_counts", "xe_normalize", "xe_probe_mma_legacy",
     "xe_stream_create", "xe_stream_submit", "xe_stream_submit_device", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
@@ -61,6 +65,15 @@ class Job(ctypes.Structure):
 class Tune(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int32), ("max_strip", ctypes.c_int32), ("k_flush", ctypes.c_int32),
                 ("n_ctas", ctypes.c_int32)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int32), ("t_bucket", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("layout", ctypes.c_int32),
+                ("pairs", ctypes.c_int32), ("odd_pairs", ctypes.c_int32), ("k_flush", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
 
 
 class StreamCfg(ctypes.Structure):
@@ -111,6 +124,8 @@ def _load():
     L.xe_correlate_batched_workspace_size.restype = sz
     L.xe_correlate_batched_workspace_size.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune)]
     L.xe_correlate_batched.argtypes = [ctypes.POINTER(Job), i32, ctypes.POINTER(Tune), vp, sz, vp]
+    L.xe_tune_table_set.argtypes = [ctypes.POINTER(TuneEntry), i32]
+    L.xe_tune_table_get.argtypes = [ctypes.POINTER(TuneEntry), i32]
     L.xe_correlate_packets_workspace_size.restype = sz
     L.xe_correlate_packets_workspace_size.argtypes = [Shape]
     L.xe_correlate_packets.argtypes = [vp, u32, u32, u64, i32, Shape, vp, ctypes.c_int, vp, vp, vp, vp, sz, vp]
@@ -291,6 +306,22 @@ def xe_correlate_batched(jobs, ws, tune=None, stream=None):
     arr = _jobs(jobs)
     _check(_L.xe_correlate_batched(arr, len(jobs), _tune(tune), _dptr(ws), _nbytes(ws), _stream(stream)),
            "xe_correlate_batched")
+
+
+def xe_tune_table_set(entries):
+    """Replaces libxe's tuning table. entries: TuneEntry objects or dicts with TuneEntry's fields."""
+    arr = (TuneEntry * max(1, len(entries)))()
+    for k, e in enumerate(entries):
+        arr[k] = e if isinstance(e, TuneEntry) else TuneEntry(**e)
+    _check(_L.xe_tune_table_set(arr, len(entries)), "xe_tune_table_set")
+
+
+def xe_tune_table_get():
+    """The tuning table as a list of dicts."""
+    n = _L.xe_tune_table_get(None, 0)
+    arr = (TuneEntry * max(1, n))()
+    n = _L.xe_tune_table_get(arr, n)
+    return [arr[k].as_dict() for k in range(n)]
 
 
 def xe_flag_counts_workspace_size(shape: Shape) -> int:

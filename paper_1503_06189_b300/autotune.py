@@ -1,29 +1,33 @@
-"""Autotuner for the correlation's work-item shape per (N, T-bucket): the single-CTA fused engine's
-strip width (1..4 tiles of 128x128 along one row of the Gram matrix per work item), and whether the
-CTA-pair engine (256x256 blocks) beats it.
+"""Autotuner of the CTA-pair engine, the engine every libxe correlation runs by default, per
+(N, T-bucket) and mode. It fills libxe's tuning table (xe_tune_entry in include/xe.h):
 
-Wider strips reuse each converted operand block across more tiles and save conversions; narrower
-strips double-buffer the tensor-memory accumulator and spread small problems over more SMs. The best
-choice depends on N (how many tiles a channel has) and T (how long each work item runs), so it is
-measured: each candidate runs on a seeded random frame of the bucket's shape on the device, timed
-with CUDA events (best of `reps`), and the winner is cached in a JSON file keyed "N<N>_T<bucket>".
+- packet mode (xe_correlate_packets and the serving loop): the work-item layout -- fold items over
+  whole 256-input super-blocks, Gram blocks with twins, or Gram blocks with wide singles -- and
+  whether the launch takes an odd number of CTA pairs;
+- frame mode (xe_correlate, xe_correlate_batched): the number of CTA pairs (fewer pairs can end a
+  launch's last round of work items more evenly) and its parity.
 
-    table = autotune.Table(path)               # loads the cache if the file exists
-    ms = table.best(N, T)                      # tunes on first use, then reads the cache
-    jobs = [(frame, vis, shape, acc, table.best(shape.n_inputs, shape.n_time)) ...]
+Each candidate runs on seeded random samples of the bucket's shape on the device (F chosen so that
+a launch has about four rounds of work items, within a few GB), timed with CUDA events (best of
+`reps`); the winner is cached as JSON under "packets_N<N>_T<bucket>" or "frames_N<N>_T<bucket>" and
+installed into libxe with xe_tune_table_set, after which every launch of that shape uses it.
+
+    table = autotune.Table(path)          # loads the cache if the file exists
+    table.tune_packets(256, 32768)        # measures on first use, then reads the cache
+    table.tune_frames(2048, 16384)
+    table.install()                       # xe_tune_table_set(all entries)
 """
 from __future__ import annotations
 
 import json
 import os
 
-import torch
-
 import paper_1503_06189_b300 as xe
 
-CANDIDATES = (1, 2, 3, 4)
-PROBE_BYTES = 256 << 20          # frame bytes of one probe launch
-PROBE_ITEMS = 4 * 148            # aim for about four waves of work items
+PAIRS = 74                      # CTA pairs resident on a B300 (one CTA per SM)
+ROUNDS = 4                      # rounds of work items a probe launch aims for
+PROBE_BYTES = 2 << 30           # samples of one probe launch at most
+PACKET_FIELDS = ("layout", "odd_pairs")
 
 
 def bucket(n_time: int) -> int:
@@ -31,53 +35,131 @@ def bucket(n_time: int) -> int:
     return 1 << max(7, (max(int(n_time), 1) - 1).bit_length())
 
 
-def key(n_inputs: int, n_time: int) -> str:
-    return f"N{int(n_inputs)}_T{bucket(n_time)}"
+def key(mode: str, n_inputs: int, n_time: int) -> str:
+    return f"{mode}_N{int(n_inputs)}_T{bucket(n_time)}"
 
 
-def _strips(n_inputs: int, ms: int) -> int:
-    nb = -(-2 * n_inputs // 128)
-    total = 0
-    for rb in range(nb):
-        wd = min(ms, nb - rb)
-        wo = min(ms, 3)
-        total += 1 + -(-(nb - rb - wd) // wo)
-    return total
+def blocks(n_inputs: int) -> int:
+    """256-row blocks of the 2N-row Gram matrix (128 inputs each)."""
+    return -(-2 * int(n_inputs) // 256)
 
 
-def measure(n_inputs: int, n_time: int, candidates=CANDIDATES, reps: int = 3, device=None) -> dict:
-    """Milliseconds per launch for each candidate strip width on a probe frame of this bucket."""
-    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+def items_per_channel(n_inputs: int, layout: int, n_time: int, packets: bool = True) -> float:
+    """Work items of one channel (the library's layouts; a twin counts half for each of its two
+    channels)."""
+    nb = blocks(n_inputs)
+    if not packets:
+        return nb * (nb + 1) / 2
+    fold = nb >= 2 and layout in (xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_FOLD)
+    if fold:
+        return nb // 2 + (nb & 1) + sum(max(0, nb - 2 * (r // 2 + 1)) for r in range(nb))
+    twin = layout == xe.XE_LAYOUT_GRAM_TWIN or (layout in (xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_GRAM)
+                                                and n_time >= 16384)
+    per_ch = (nb - 1) + (nb - 1) * (nb - 2) // 2
+    return per_ch + (0.5 if twin else 1.0)
+
+
+def packet_candidates(n_inputs: int) -> list[dict]:
+    """Layouts worth measuring in packet mode, each with and without an odd pair count."""
+    layouts = [xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM] if blocks(n_inputs) >= 2 else \
+        [xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE]
+    return [dict(layout=lay, pairs=0, odd_pairs=odd, k_flush=0) for lay in layouts for odd in (0, 1)]
+
+
+def frame_candidates(n_inputs: int, n_chan: int) -> list[dict]:
+    """Pair counts worth measuring in frame mode: all, an odd count, and the smallest count that
+    keeps the number of rounds of work items (fewer pairs finish a ragged last round together)."""
+    items = int(items_per_channel(n_inputs, xe.XE_LAYOUT_AUTO, 0, packets=False)) * n_chan
+    rounds = -(-items // PAIRS)
+    even = -(-items // rounds)
+    cands = [dict(layout=xe.XE_LAYOUT_AUTO, pairs=0, odd_pairs=0, k_flush=0),
+             dict(layout=xe.XE_LAYOUT_AUTO, pairs=0, odd_pairs=1, k_flush=0)]
+    if even < PAIRS:
+        cands.append(dict(layout=xe.XE_LAYOUT_AUTO, pairs=even, odd_pairs=0, k_flush=0))
+    return cands
+
+
+def probe_chan(n_inputs: int, n_time: int, per_channel: float, multiple: int) -> int:
+    """Channels of a probe launch: about ROUNDS rounds of work items within PROBE_BYTES."""
+    f = max(1, round(ROUNDS * PAIRS / max(per_channel, 1e-9)))
+    f = min(f, max(1, PROBE_BYTES // (n_time * n_inputs)))
+    return max(multiple, f // multiple * multiple)
+
+
+def _time(fn, reps: int) -> float:
+    import torch
+
+    fn()                                                           # warm-up
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def measure_packets(n_inputs: int, n_time: int, candidates=None, reps: int = 3) -> list[tuple[dict, float]]:
+    """Milliseconds per xe_correlate_packets call for each candidate entry (zero-copy, accumulating)."""
+    import torch
+
+    import synth
+
     T = bucket(n_time)
-    per_chan = T * n_inputs
-    F = max(1, min(PROBE_BYTES // per_chan, -(-PROBE_ITEMS // _strips(n_inputs, max(candidates)))))
-    g = torch.Generator(device=dev)
-    g.manual_seed(n_inputs * 131 + T)
-    frame = torch.randint(0, 256, (T, F, n_inputs), generator=g, device=dev, dtype=torch.int32).to(torch.uint8)
+    cands = candidates or packet_candidates(n_inputs)
+    F = probe_chan(n_inputs, T, min(items_per_channel(n_inputs, c["layout"], T) for c in cands), 8)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    frame = synth.uniform_frame_torch(n_inputs, F, T, n_inputs * 131 + T, device=dev)
+    pk = synth.packetize_torch(frame, 0, 1)
+    del frame
     s = xe.Shape(n_inputs, F, T)
-    vis = torch.empty((F, xe.npairs(n_inputs), 2), dtype=torch.int32, device=dev)
-    out = {}
-    for ms in list(candidates) + ["pair"]:
-        pair = ms == "pair"
-        jobs = [(frame, vis, s, False, 0 if pair else ms)]
-        tune = dict(engine=xe.XE_ENGINE_FUSED_PAIR if pair else xe.XE_ENGINE_FUSED, max_strip=0 if pair else ms,
-                    k_flush=0, n_ctas=0)
-        ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device=dev)
-        xe.xe_correlate_batched(jobs, ws, tune)                       # warm-up
-        best = float("inf")
-        for _ in range(reps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            xe.xe_correlate_batched(jobs, ws, tune)
-            e1.record()
-            torch.cuda.synchronize(dev)
-            best = min(best, e0.elapsed_time(e1))
-        out[ms] = best
+    vis = torch.zeros((F, xe.npairs(n_inputs), 2), dtype=torch.int32, device=dev)
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device=dev)
+    lost = torch.zeros(F, dtype=torch.int32, device=dev)
+    stats = torch.zeros(5, dtype=torch.int32, device=dev)
+    ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device=dev)
+    saved = xe.xe_tune_table_get()
+    out = []
+    try:
+        for c in cands:
+            xe.xe_tune_table_set([dict(c, n_inputs=n_inputs, t_bucket=T, mode=xe.XE_TUNE_PACKETS)])
+            ms = _time(lambda: xe.xe_correlate_packets(pk, pk.shape[0], pk.shape[1], 0, 1, s, vis, True, filled, lost,
+                                                       stats, ws), reps)
+            out.append((c, ms))
+    finally:
+        xe.xe_tune_table_set(saved)
+    return out
+
+
+def measure_frames(n_inputs: int, n_time: int, candidates=None, reps: int = 3) -> list[tuple[dict, float]]:
+    """Milliseconds per xe_correlate_batched launch (one job of the bucket's shape) per candidate."""
+    import torch
+
+    import synth
+
+    T = bucket(n_time)
+    F = probe_chan(n_inputs, T, items_per_channel(n_inputs, xe.XE_LAYOUT_AUTO, T, packets=False), 1)
+    cands = candidates or frame_candidates(n_inputs, F)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    frame = synth.uniform_frame_torch(n_inputs, F, T, n_inputs * 137 + T, device=dev)
+    vis = torch.zeros((F, xe.npairs(n_inputs), 2), dtype=torch.int32, device=dev)
+    jobs = [(frame, vis, xe.Shape(n_inputs, F, T), False)]
+    ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs), dtype=torch.uint8, device=dev)
+    saved = xe.xe_tune_table_get()
+    out = []
+    try:
+        for c in cands:
+            xe.xe_tune_table_set([dict(c, n_inputs=n_inputs, t_bucket=T, mode=xe.XE_TUNE_FRAMES)])
+            out.append((c, _time(lambda: xe.xe_correlate_batched(jobs, ws), reps)))
+    finally:
+        xe.xe_tune_table_set(saved)
     return out
 
 
 class Table:
-    """Cached strip widths per (N, T-bucket), persisted as JSON at `path` (None: in memory only)."""
+    """Tuned entries per (mode, N, T-bucket), persisted as JSON at `path` (None: in memory only)."""
 
     def __init__(self, path: str | None = None):
         self.path = path
@@ -86,24 +168,33 @@ class Table:
             with open(path) as f:
                 self.entries = json.load(f)
 
-    def _entry(self, n_inputs: int, n_time: int) -> dict:
-        k = key(n_inputs, n_time)
+    def _tune(self, mode: str, n_inputs: int, n_time: int) -> dict:
+        k = key(mode, n_inputs, n_time)
         if k not in self.entries:
-            ms = measure(n_inputs, n_time)
-            strips = {c: v for c, v in ms.items() if c != "pair"}
-            win = min(strips, key=strips.get)
-            self.entries[k] = {"max_strip": int(win), "pair_wins": bool(ms["pair"] < strips[win]),
-                               "ms": {str(c): round(v, 4) for c, v in ms.items()}}
+            res = (measure_packets if mode == "packets" else measure_frames)(n_inputs, n_time)
+            best, best_ms = min(res, key=lambda r: r[1])
+            self.entries[k] = {"n_inputs": int(n_inputs), "t_bucket": bucket(n_time),
+                               "mode": xe.XE_TUNE_PACKETS if mode == "packets" else xe.XE_TUNE_FRAMES,
+                               "layout": int(best["layout"]), "pairs": int(best["pairs"]),
+                               "odd_pairs": int(best["odd_pairs"]), "k_flush": int(best["k_flush"]),
+                               "ms": round(best_ms, 4),
+                               "measured": [dict(c, ms=round(ms, 4)) for c, ms in res]}
             self.save()
         return self.entries[k]
 
-    def best(self, n_inputs: int, n_time: int) -> int:
-        """Best strip width of the single-CTA fused engine for this bucket."""
-        return int(self._entry(n_inputs, n_time)["max_strip"])
+    def tune_packets(self, n_inputs: int, n_time: int) -> dict:
+        return self._tune("packets", n_inputs, n_time)
 
-    def best_engine(self, n_inputs: int, n_time: int) -> int:
-        """XE_ENGINE_FUSED_PAIR if the CTA-pair engine beat every strip width, else XE_ENGINE_FUSED."""
-        return xe.XE_ENGINE_FUSED_PAIR if self._entry(n_inputs, n_time)["pair_wins"] else xe.XE_ENGINE_FUSED
+    def tune_frames(self, n_inputs: int, n_time: int) -> dict:
+        return self._tune("frames", n_inputs, n_time)
+
+    def c_entries(self) -> list[dict]:
+        fields = ("n_inputs", "t_bucket", "mode", "layout", "pairs", "odd_pairs", "k_flush")
+        return [{f: e[f] for f in fields} for e in self.entries.values()]
+
+    def install(self):
+        """Loads every entry into libxe's tuning table."""
+        xe.xe_tune_table_set(self.c_entries())
 
     def save(self):
         if not self.path:

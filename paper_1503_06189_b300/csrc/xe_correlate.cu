@@ -1641,6 +1641,29 @@ static int check_tune(const xe_tune &t) {
     return XE_OK;
 }
 
+// ----------------------------------------------------------------------------- tuning table
+
+static std::mutex g_tune_mu;
+static xe_tune_entry g_tune[XE_TUNE_MAX_ENTRIES];
+static int g_tune_n = 0;
+
+static int t_bucket_of(int t) {
+    int b = 128;
+    while (b < t && b < (1 << 30)) b <<= 1;
+    return b;
+}
+
+// The table's entry for jobs of shape s, copied into *e; false if there is none. Caller holds g_tune_mu.
+static bool tune_lookup(const xe_shape &s, int mode, xe_tune_entry *e) {
+    const int b = t_bucket_of(s.n_time);
+    for (int k = 0; k < g_tune_n; ++k)
+        if (g_tune[k].n_inputs == s.n_inputs && g_tune[k].t_bucket == b && g_tune[k].mode == mode) {
+            *e = g_tune[k];
+            return true;
+        }
+    return false;
+}
+
 static constexpr size_t kWsHeader = 1024;   // work-item counter; operands start 1 KiB in
 
 using PacketSrc = xe::packet_src;
@@ -1746,6 +1769,30 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     int *status = status_word();
     if (!status) return XE_ECUDA;
 
+    // the tuning table's entries of the jobs (pair engine); the launch-wide choices come from the
+    // entry of the job with the most work
+    xe_tune_entry ent[XE_MAX_JOBS];
+    bool has_ent[XE_MAX_JOBS] = {};
+    xe_tune_entry launch_ent{};
+    bool has_launch_ent = false;
+    if (engine == kFusedPair) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        double best = -1.0;
+        for (int j = 0; j < n_jobs; ++j) {
+            has_ent[j] = tune_lookup(jobs[j].s, pk ? XE_TUNE_PACKETS : XE_TUNE_FRAMES, &ent[j]);
+            const double w = (double)jobs[j].s.n_chan * (double)npairs(jobs[j].s.n_inputs) * (double)jobs[j].s.n_time;
+            if (w > best) {
+                best = w;
+                has_launch_ent = has_ent[j];
+                if (has_ent[j]) launch_ent = ent[j];
+            }
+        }
+    }
+    if (has_launch_ent) {
+        if (!(tune_in && tune_in->k_flush) && launch_ent.k_flush) tune.k_flush = launch_ent.k_flush;
+        if (!(tune_in && tune_in->n_ctas) && launch_ent.pairs) tune.n_ctas = 2 * launch_ent.pairs;
+    }
+
     static Params hp;    // large; built under a lock
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
@@ -1808,7 +1855,8 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         if (engine == kFusedPair) {             // 256x256 blocks on or above the diagonal
             d.nb = (g.nb + 1) / 2;
             d.fold = 0;
-            if (pk && d.nb >= 2) {
+            const int layout = has_ent[j] ? ent[j].layout : XE_LAYOUT_AUTO;
+            if (pk && d.nb >= 2 && (layout == XE_LAYOUT_AUTO || layout == XE_LAYOUT_FOLD)) {
                 // fold layout: per channel S2 / 2 fold items, a Gram diagonal single for an odd last
                 // block, and the Gram blocks (R, C) between different super-blocks (R / 2 < C / 2)
                 d.fold = 1;
@@ -1825,7 +1873,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
                 // channel keeps its diagonal single), short ones each channel's as a wide single
                 d.doubles = d.nb - 1;
                 d.offdiag = (d.nb - 1) * (d.nb - 2) / 2;
-                d.twin = s.n_time >= kTwinMinTime ? 1 : 0;
+                d.twin = layout == XE_LAYOUT_GRAM_TWIN ? 1
+                         : layout == XE_LAYOUT_GRAM_WIDE ? 0
+                         : (s.n_time >= kTwinMinTime ? 1 : 0);
                 if (d.twin) {
                     d.strips = 2 * (d.doubles + d.offdiag) + 1;
                     job_items = (int64_t)(s.n_chan / 2) * d.strips + (s.n_chan % 2) * (d.doubles + d.offdiag + 1);
@@ -1901,8 +1951,13 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     const int smem = 1024 + hp.op_stages * hp.slots * op_slot + hp.pk_stages * hp.slots * pk_slot + bar_bytes + staging;
     XE_TRY_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), st));
     if (engine == kFusedPair)
-        return pk ? launch_pair<true>(hp, items, tune.n_ctas, smem, !all_fold, st)
-                  : launch_pair<false>(hp, items, tune.n_ctas, smem, false, st);
+    {
+        // the Gram layout's doubles and singles alternate best on an odd pair count; fold items are alike
+        bool odd = pk && !all_fold;
+        if (has_launch_ent && launch_ent.odd_pairs >= 0) odd = launch_ent.odd_pairs == 1;
+        return pk ? launch_pair<true>(hp, items, tune.n_ctas, smem, odd, st)
+                  : launch_pair<false>(hp, items, tune.n_ctas, smem, odd, st);
+    }
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     switch (engine) {
         case kUnpackedK: return launch_gemm<kUnpackedK>(hp, ctas, smem, st);
@@ -1940,6 +1995,33 @@ int xe_correlate(const uint8_t *frame, xe_shape s, int32_t *vis, int accumulate,
                  void *stream) {
     xe_job j{frame, vis, s, accumulate ? 1 : 0, 0};
     return corr::run_batched(&j, 1, nullptr, ws, ws_bytes, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int xe_tune_table_set(const xe_tune_entry *entries, int32_t n) {
+    if (n < 0 || n > XE_TUNE_MAX_ENTRIES || (n > 0 && !entries)) return XE_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        const xe_tune_entry &e = entries[k];
+        const bool pow2 = e.t_bucket >= 128 && (e.t_bucket & (e.t_bucket - 1)) == 0;
+        if (e.n_inputs < 16 || e.n_inputs > 4096 || e.n_inputs % 16 || !pow2 || e.mode < XE_TUNE_PACKETS ||
+            e.mode > XE_TUNE_FRAMES || e.layout < XE_LAYOUT_AUTO ||
+            e.layout > XE_LAYOUT_FOLD || e.pairs < 0 || e.pairs > 4096 || e.odd_pairs < -1 || e.odd_pairs > 1 ||
+            e.k_flush < 0 || e.k_flush > corr::kMaxKFlush || e.k_flush % corr::kKtMax)
+            return XE_EINVAL;
+        for (int k2 = 0; k2 < k; ++k2)
+            if (entries[k2].n_inputs == e.n_inputs && entries[k2].t_bucket == e.t_bucket && entries[k2].mode == e.mode)
+                return XE_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(corr::g_tune_mu);
+    for (int k = 0; k < n; ++k) corr::g_tune[k] = entries[k];
+    corr::g_tune_n = n;
+    return XE_OK;
+}
+
+int xe_tune_table_get(xe_tune_entry *out, int32_t cap) {
+    std::lock_guard<std::mutex> lk(corr::g_tune_mu);
+    if (out)
+        for (int k = 0; k < std::min<int>(cap, corr::g_tune_n); ++k) out[k] = corr::g_tune[k];
+    return corr::g_tune_n;
 }
 
 size_t xe_correlate_batched_workspace_size(const xe_job *jobs, int32_t n_jobs, const xe_tune *tune) {

@@ -1,6 +1,7 @@
-"""Host logic of the autotuner (no GPU): T buckets, cache keys, work-item counts, the choice between
-strip widths and the CTA-pair engine, and the JSON cache. The device measurement is replaced by a
-fake that returns fixed timings and counts its calls."""
+"""Host logic of the autotuner (no GPU): T buckets, cache keys, work-item counts per layout (against
+the enumeration the kernel uses, written out), candidate sets, the choice of the fastest candidate,
+the JSON cache, and installing the table into libxe (a host-only call). The device measurement is
+replaced by a fake that returns fixed timings and counts its calls."""
 import json
 
 import pytest
@@ -15,19 +16,57 @@ def test_bucket_is_the_power_of_two_at_or_above_t(t, b):
     assert autotune.bucket(t) == b
 
 
-def test_key_names_inputs_and_bucket():
-    assert autotune.key(256, 4000) == "N256_T4096"
-    assert autotune.key(2048, 1024) == "N2048_T1024"
+def test_key_names_mode_inputs_and_bucket():
+    assert autotune.key("packets", 256, 4000) == "packets_N256_T4096"
+    assert autotune.key("frames", 2048, 1024) == "frames_N2048_T1024"
 
 
-@pytest.mark.parametrize("n", [16, 64, 100 * 16, 256, 512, 2048])
-def test_strip_counts_special_cases(n):
-    nb = -(-2 * n // 128)                                   # 128-row blocks of the 2N-row Gram matrix
-    assert autotune._strips(n, 1) == nb * (nb + 1) // 2     # one tile per strip: every tile on/above the diagonal
-    if nb <= 3:
-        assert autotune._strips(n, 4) == nb                 # each row's tiles fit one strip
-    counts = [autotune._strips(n, ms) for ms in (1, 2, 3, 4)]
-    assert counts == sorted(counts, reverse=True)           # wider strips never need more work items
+def _fold_cover(nb):
+    """Blocks (R, C) of a channel covered by the fold layout, item by item (fold items cover three)."""
+    cover = []
+    for q in range(nb // 2):
+        cover += [(2 * q, 2 * q), (2 * q, 2 * q + 1), (2 * q + 1, 2 * q + 1)]
+    if nb & 1:
+        cover.append((nb - 1, nb - 1))
+    for r in range(nb):
+        for c in range(2 * (r // 2 + 1), nb):
+            cover.append((r, c))
+    return cover
+
+
+@pytest.mark.parametrize("n", [144, 256, 272, 384, 512, 640, 2048, 4096])
+def test_fold_layout_covers_every_block_once(n):
+    nb = autotune.blocks(n)
+    cover = _fold_cover(nb)
+    assert sorted(cover) == sorted((r, c) for r in range(nb) for c in range(r, nb))
+    fold_items = nb // 2
+    assert autotune.items_per_channel(n, xe.XE_LAYOUT_FOLD, 4096) == len(cover) - 2 * fold_items
+
+
+def test_items_per_channel_of_the_gram_layouts():
+    # N = 256: one double and a twin half or a wide single per channel
+    assert autotune.items_per_channel(256, xe.XE_LAYOUT_GRAM_TWIN, 4096) == 1.5
+    assert autotune.items_per_channel(256, xe.XE_LAYOUT_GRAM_WIDE, 32768) == 2.0
+    assert autotune.items_per_channel(256, xe.XE_LAYOUT_GRAM, 32768) == 1.5    # twins from T >= 16384
+    assert autotune.items_per_channel(256, xe.XE_LAYOUT_AUTO, 4096) == 1       # fold at N > 128
+    assert autotune.items_per_channel(64, xe.XE_LAYOUT_AUTO, 4096) == 1        # one block: wide single
+    assert autotune.items_per_channel(2048, xe.XE_LAYOUT_AUTO, 0, packets=False) == 136
+
+
+def test_candidate_sets():
+    p256 = autotune.packet_candidates(256)
+    assert {c["layout"] for c in p256} == {xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM}
+    assert {c["odd_pairs"] for c in p256} == {0, 1}
+    p64 = autotune.packet_candidates(64)
+    assert {c["layout"] for c in p64} == {xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE}
+    f = autotune.frame_candidates(256, 100)           # 300 blocks: 5 rounds on 74 pairs, 60 pairs suffice
+    assert {c["pairs"] for c in f} == {0, 60}
+
+
+def test_probe_channels_aim_for_rounds_within_bytes():
+    assert autotune.probe_chan(256, 4096, 1, 8) == 296
+    assert autotune.probe_chan(2048, 32768, 136, 1) == 2
+    assert autotune.probe_chan(256, 1 << 20, 1, 8) == 8               # capped by the probe's bytes
 
 
 class FakeMeasure:
@@ -37,39 +76,45 @@ class FakeMeasure:
 
     def __call__(self, n_inputs, n_time, *args, **kwargs):
         self.calls.append((n_inputs, autotune.bucket(n_time)))
-        return dict(self.timings)
+        return [(dict(c), ms) for c, ms in self.timings]
 
 
-def test_table_picks_fastest_strip_and_caches(tmp_path, monkeypatch):
-    fake = FakeMeasure({1: 3.0, 2: 1.5, 3: 2.0, 4: 1.7, "pair": 2.5})
-    monkeypatch.setattr(autotune, "measure", fake)
+def test_table_picks_fastest_candidate_caches_and_installs(tmp_path, monkeypatch):
+    fold = dict(layout=xe.XE_LAYOUT_FOLD, pairs=0, odd_pairs=0, k_flush=0)
+    gram = dict(layout=xe.XE_LAYOUT_GRAM, pairs=0, odd_pairs=1, k_flush=0)
+    fake = FakeMeasure([(fold, 4.6), (gram, 5.1)])
+    monkeypatch.setattr(autotune, "measure_packets", fake)
+    monkeypatch.setattr(autotune, "measure_frames", FakeMeasure([(dict(fold, layout=0, pairs=64), 9.0)]))
     path = str(tmp_path / "sub" / "table.json")
     t = autotune.Table(path)
-    assert t.best(256, 4000) == 2
-    assert t.best_engine(256, 4000) == xe.XE_ENGINE_FUSED   # pair (2.5) slower than strip 2 (1.5)
-    assert t.best(256, 4096) == 2                           # same bucket: no new measurement
-    assert fake.calls == [(256, 4096)]
-    t.best(256, 4097)                                       # next bucket
-    assert fake.calls == [(256, 4096), (256, 8192)]
+    e = t.tune_packets(256, 32768)
+    assert e["layout"] == xe.XE_LAYOUT_FOLD and e["ms"] == 4.6 and len(e["measured"]) == 2
+    t.tune_packets(256, 20000)                                     # same bucket: no new measurement
+    assert fake.calls == [(256, 32768)]
+    t.tune_frames(2048, 16384)
     saved = json.load(open(path))
-    assert set(saved) == {"N256_T4096", "N256_T8192"} and saved["N256_T4096"]["max_strip"] == 2
+    assert set(saved) == {"packets_N256_T32768", "frames_N2048_T16384"}
+    t2 = autotune.Table(path)                                      # reloaded from the cache
+    assert t2.tune_packets(256, 32768)["layout"] == xe.XE_LAYOUT_FOLD and fake.calls == [(256, 32768)]
+    try:
+        t2.install()
+        got = {(e["n_inputs"], e["t_bucket"], e["mode"]): e for e in xe.xe_tune_table_get()}
+        assert got[(256, 32768, xe.XE_TUNE_PACKETS)]["layout"] == xe.XE_LAYOUT_FOLD
+        assert got[(2048, 16384, xe.XE_TUNE_FRAMES)]["pairs"] == 64
+    finally:
+        xe.xe_tune_table_set([])
 
 
-def test_table_prefers_pair_engine_when_faster(monkeypatch):
-    monkeypatch.setattr(autotune, "measure", FakeMeasure({1: 3.0, 2: 2.0, 3: 2.2, 4: 2.1, "pair": 1.2}))
-    t = autotune.Table(None)                                # in memory only
-    assert t.best_engine(2048, 32768) == xe.XE_ENGINE_FUSED_PAIR
-    assert t.best(2048, 32768) == 2
-
-
-def test_table_reloads_without_measuring(tmp_path, monkeypatch):
-    monkeypatch.setattr(autotune, "measure", FakeMeasure({1: 1.0, 2: 2.0, 3: 3.0, 4: 4.0, "pair": 5.0}))
-    path = str(tmp_path / "table.json")
-    autotune.Table(path).best(128, 1024)
-
-    def no_measure(*a, **k):
-        raise AssertionError("a cached bucket was measured again")
-
-    monkeypatch.setattr(autotune, "measure", no_measure)
-    t = autotune.Table(path)
-    assert t.best(128, 1000) == 1 and t.best_engine(128, 1000) == xe.XE_ENGINE_FUSED
+def test_tune_table_rejects_bad_entries():
+    good = dict(n_inputs=256, t_bucket=4096, mode=0, layout=4, pairs=0, odd_pairs=-1, k_flush=0)
+    for bad in (dict(good, t_bucket=4000), dict(good, n_inputs=250), dict(good, layout=9), dict(good, mode=2),
+                dict(good, k_flush=100), dict(good, odd_pairs=2)):
+        with pytest.raises(xe.XeError) as e:
+            xe.xe_tune_table_set([bad])
+        assert e.value.status == xe.XE_EINVAL
+    with pytest.raises(xe.XeError):
+        xe.xe_tune_table_set([good, dict(good)])                  # two entries for one (N, bucket, mode)
+    xe.xe_tune_table_set([good, dict(good, mode=1)])
+    assert len(xe.xe_tune_table_get()) == 2
+    xe.xe_tune_table_set([])
+    assert xe.xe_tune_table_get() == []

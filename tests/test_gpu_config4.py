@@ -1,7 +1,8 @@
-"""Uneven batch in one launch (24 jobs, N 64..2048, F 16..256, T 1024..32768, signal model), with the
-strip width of every job picked by the autotuner for its (N, T-bucket). Each job is checked against
-the oracle: whole channels where that is cheap on the CPU, sampled visibilities otherwise; and every
-channel of every job equals a separate single-job launch (GPU)."""
+"""Uneven batch in one launch (24 jobs, N 64..2048, F 16..256, T 1024..32768, signal model) on the
+default CTA-pair engine, with the launch shape of every (N, T-bucket) picked by the autotuner and
+installed in libxe's tuning table. Each job is checked against the oracle: whole channels where that
+is cheap on the CPU, sampled visibilities otherwise; and every channel of every job equals a separate
+single-job launch (GPU)."""
 import numpy as np
 import pytest
 import torch
@@ -14,23 +15,34 @@ from paper_1503_06189_b300 import autotune
 pytestmark = pytest.mark.gpu
 
 
-def test_uneven_batch_autotuned(tmp_path):
+def test_uneven_batch_autotuned(tmp_path, monkeypatch):
     dev = torch.device("cuda")
     shapes = synth.config4_shapes()
+    monkeypatch.setattr(autotune, "PROBE_BYTES", 256 << 20)       # small probes: the test times the table, too
     table = autotune.Table(str(tmp_path / "autotune.json"))
-    frames, vis, jobs = [], [], []
-    for k, (N, F, T) in enumerate(shapes):
-        chunk = max(1, (1 << 27) // (T * N))
-        fr = synth.signal_frame_torch(N, F, T, 4000 + k, device=dev, chunk=chunk)
-        v = torch.full((F, xe.npairs(N), 2), -1, dtype=torch.int32, device=dev)
-        frames.append(fr)
-        vis.append(v)
-        jobs.append((fr, v, xe.Shape(N, F, T), False, table.best(N, T)))
-    assert len(table.entries) >= 1 and all(1 <= e["max_strip"] <= 4 for e in table.entries.values())
-    tune = dict(engine=xe.XE_ENGINE_FUSED, max_strip=0, k_flush=0, n_ctas=0)   # per-job strip widths
-    ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs, tune), dtype=torch.uint8, device=dev)
-    xe.xe_correlate_batched(jobs, ws, tune)
-    torch.cuda.synchronize()
+    for N, F, T in shapes:
+        table.tune_frames(N, T)
+    table.install()
+    try:
+        installed = xe.xe_tune_table_get()
+        assert len(installed) == len({(N, autotune.bucket(T)) for N, F, T in shapes})
+        frames, vis, jobs = [], [], []
+        for k, (N, F, T) in enumerate(shapes):
+            chunk = max(1, (1 << 27) // (T * N))
+            fr = synth.signal_frame_torch(N, F, T, 4000 + k, device=dev, chunk=chunk)
+            v = torch.full((F, xe.npairs(N), 2), -1, dtype=torch.int32, device=dev)
+            frames.append(fr)
+            vis.append(v)
+            jobs.append((fr, v, xe.Shape(N, F, T), False))
+        ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs), dtype=torch.uint8, device=dev)
+        xe.xe_correlate_batched(jobs, ws)                          # default engine, tuned launch shape
+        torch.cuda.synchronize()
+        _check_jobs(shapes, frames, vis, dev)
+    finally:
+        xe.xe_tune_table_set([])
+
+
+def _check_jobs(shapes, frames, vis, dev):
     rng = np.random.default_rng(44)
     for k, ((N, F, T), fr, v) in enumerate(zip(shapes, frames, vis)):
         # every channel: equal to the job launched alone on the default (CTA-pair) engine
