@@ -13,6 +13,8 @@ Function / paper passage:
   counts_from_mask      n_ij by brute force over the sample mask      Sec. II-C
   counts_from_counters  n_ij by the loss / flag / intersection counters  Sec. II-C
   normalize       V / n_ij                                            Sec. II-C
+  time_shift      per-input integer sample delay (reading)           Fig. 4 caption
+  time_shift_counts     the delay's samples without data as counters  Fig. 4 caption, Sec. II-C
 """
 from __future__ import annotations
 
@@ -65,6 +67,10 @@ class Oracle:
                                               ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]
         L.xo_normalize.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_void_p]
+        L.xo_time_shift.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.c_void_p]
+        L.xo_time_shift_counts.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                           ctypes.c_void_p]
         L.xo_pidx.restype = ctypes.c_int64
         L.xo_pidx.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.xo_npairs.restype = ctypes.c_int64
@@ -168,6 +174,25 @@ class Oracle:
             raise ValueError("xo_normalize: invalid arguments")
         return out
 
+    def time_shift(self, frame: np.ndarray, delays) -> np.ndarray:
+        """frame uint8 [T][F][N], delays int [N] (0 <= d <= T) -> the shifted frame."""
+        frame = np.ascontiguousarray(frame, dtype=np.uint8)
+        T, F, N = frame.shape
+        d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+        out = np.full_like(frame, 0xA5)
+        if d.shape != (N,) or self.L.xo_time_shift(_ptr(frame), N, F, T, _ptr(d), _ptr(out)) != OK:
+            raise ValueError("xo_time_shift: invalid arguments")
+        return out
+
+    def time_shift_counts(self, delays, n_inputs: int, n_chan: int, flag_count=None, flag_pairs=None):
+        """Adds the shift's samples without data to (flag_count [F][N], flag_pairs [F][P])."""
+        d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+        c = np.zeros((n_chan, n_inputs), np.uint32) if flag_count is None else flag_count
+        x = np.zeros((n_chan, self.npairs(n_inputs)), np.uint32) if flag_pairs is None else flag_pairs
+        if d.shape != (n_inputs,) or self.L.xo_time_shift_counts(_ptr(d), n_inputs, n_chan, _ptr(c), _ptr(x)) != OK:
+            raise ValueError("xo_time_shift_counts: invalid arguments")
+        return c, x
+
 
 def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
@@ -225,3 +250,11 @@ def counts_from_counters(t_int, lost, n_inputs, flag_count=None, flag_pairs=None
 
 def normalize(vis, n):
     return default().normalize(vis, n)
+
+
+def time_shift(frame, delays):
+    return default().time_shift(frame, delays)
+
+
+def time_shift_counts(delays, n_inputs, n_chan, flag_count=None, flag_pairs=None):
+    return default().time_shift_counts(delays, n_inputs, n_chan, flag_count, flag_pairs)

@@ -277,6 +277,48 @@ int xo_normalize(const int64_t *vis, const uint32_t *n, int N, int F, float *out
     return XO_OK;
 }
 
+/*
+ * Time shifting. Fig. 4's caption names "time shifting" among the optional GPU stages between the
+ * frame's transfer and the correlation, and the paper defines it no further. Reading used: every
+ * input n of every channel is delayed by an integer number of samples d[n], 0 <= d[n] <= T:
+ *   out[t][f][n] = in[t - d[n]][f][n]  for t >= d[n],
+ *   out[t][f][n] = 0 (no data)          for t <  d[n].
+ * in, out: uint8 [T][F][N] (distinct buffers); delays: int32 [N].
+ */
+int xo_time_shift(const uint8_t *in, int N, int F, int T, const int32_t *delays, uint8_t *out) {
+    if (!in || !out || !delays || N <= 0 || F <= 0 || T < 0) return XO_EINVAL;
+    for (int n = 0; n < N; ++n)
+        if (delays[n] < 0 || delays[n] > T) return XO_EINVAL;
+    for (int t = 0; t < T; ++t)
+        for (int f = 0; f < F; ++f)
+            for (int n = 0; n < N; ++n) {
+                const int src = t - delays[n];
+                out[((size_t)t * F + f) * N + n] = src >= 0 ? in[((size_t)src * F + f) * N + n] : 0;
+            }
+    return XO_OK;
+}
+
+/*
+ * The shift's samples without data, in the form of the per-input counters of Sec. II-C (added to
+ * flag_count and flag_pairs, which xo_counts_from_counters takes): input n of every channel has
+ * its first d[n] samples without data, c[f][n] += d[n]; inputs i and j both lack their first
+ * min(d[i], d[j]) samples, x[f][p(i,j)] += min(d[i], d[j]).
+ * flag_count: uint32 [F][N], flag_pairs: uint32 [F][P].
+ */
+int xo_time_shift_counts(const int32_t *delays, int N, int F, uint32_t *flag_count, uint32_t *flag_pairs) {
+    if (!delays || !flag_count || !flag_pairs || N <= 0 || F <= 0) return XO_EINVAL;
+    const int64_t P = xo_npairs(N);
+    for (int f = 0; f < F; ++f)
+        for (int i = 0; i < N; ++i) {
+            flag_count[(size_t)f * N + i] += (uint32_t)delays[i];
+            for (int j = i; j < N; ++j) {
+                const int m = delays[i] < delays[j] ? delays[i] : delays[j];
+                flag_pairs[(size_t)f * P + xo_pidx(i, j, N)] += (uint32_t)m;
+            }
+        }
+    return XO_OK;
+}
+
 /* Threads the OpenMP runtime will use (reported beside the CPU baseline). */
 int xo_threads(void) {
 #ifdef _OPENMP

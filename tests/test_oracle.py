@@ -197,7 +197,7 @@ def pin_single_source(o):
     """x_n(t) = g_n s(t) gives V = (sum_t |s(t)|^2) g_i conj(g_j)."""
     rng = np.random.default_rng(16)
     N, T = 12, 400
-    g = rng.integers(-2, 3, N) + 1j * rng.integers(-2, 3, N)
+    g = rng.integers(-1, 2, N) + 1j * rng.integers(-1, 2, N)      # |Re, Im of g s| <= 6
     s = rng.integers(-2, 2, T) + 1j * rng.integers(-1, 2, T)
     x = s[:, None] * g[None, :]                   # components within [-8, 7]
     fr = synth.pack(x.real.astype(int), x.imag.astype(int)).reshape(T, 1, N)
@@ -440,12 +440,90 @@ def pin_flag_counts_give_mask_counts(o):
     np.testing.assert_array_equal(o.counts_from_counters(T, lost, N, c, x), o.counts_from_mask(valid.astype(np.uint8)))
 
 
+def pin_time_shift_brute_force(o, seed=40):
+    """Time shift (reading of the Fig. 4 stage): each output byte by its definition written out in
+    Python; zero delays are the identity; the delay is a shift towards later samples."""
+    rng = np.random.default_rng(seed)
+    T, F, N = 37, 3, 16
+    fr = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    d = rng.integers(0, T + 1, N)
+    d[0], d[1] = 0, T
+    got = o.time_shift(fr, d)
+    want = np.zeros_like(fr)
+    for t in range(T):
+        for f in range(F):
+            for n in range(N):
+                if t >= d[n]:
+                    want[t, f, n] = fr[t - d[n], f, n]
+    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(o.time_shift(fr, np.zeros(N, int)), fr)
+    one = o.time_shift(fr, np.ones(N, int))
+    np.testing.assert_array_equal(one[1:], fr[:-1])
+    assert not one[0].any()
+
+
+def pin_time_shift_constant_input(o):
+    """A constant input shifted by d_n correlates to (T - max(d_i, d_j)) c_i conj(c_j) exactly."""
+    rng = np.random.default_rng(41)
+    N, F, T = 16, 2, 300
+    c = rng.integers(-8, 8, N) + 1j * rng.integers(-8, 8, N)
+    d = rng.integers(0, 120, N)
+    v, st = o.correlate(o.time_shift(synth.constant_frame(c, F, T), d))
+    assert st == oracle.OK
+    for i in range(N):
+        for j in range(i, N):
+            want = (T - max(d[i], d[j])) * c[i] * np.conj(c[j])
+            p = o.pidx(i, j, N)
+            assert v[0, p, 0] == want.real and v[0, p, 1] == want.imag, (i, j)
+
+
+def pin_time_shift_aligns_delayed_source(o):
+    """The stage's purpose: a common signal s arriving at input n tau_n samples late
+    (x_n(t) = g_n s(t - tau_n)) is re-aligned by delays d_n = D - tau_n (D = max tau): every input
+    then carries g_n s(t - D), and V[i,j] = g_i conj(g_j) sum over t >= max(d_i, d_j) of |s(t - D)|^2."""
+    rng = np.random.default_rng(42)
+    N, T, D = 16, 400, 40
+    tau = rng.integers(0, D + 1, N)
+    tau[0] = D
+    g = rng.integers(-1, 2, N) + 1j * rng.integers(-1, 2, N)      # |Re, Im of g s| <= 6
+    s_t = rng.integers(-3, 4, T + D) + 1j * rng.integers(-3, 4, T + D)   # s(t) for t = -D .. T - 1
+    x = np.stack([g[n] * s_t[D - tau[n]:D - tau[n] + T] for n in range(N)], axis=1)   # [T][N]
+    fr = synth.pack(x.real.astype(np.int64), x.imag.astype(np.int64))[:, None, :]
+    d = D - tau
+    v, st = o.correlate(o.time_shift(fr, d))
+    assert st == oracle.OK
+    for i in range(N):
+        for j in range(i, N):
+            t0 = max(d[i], d[j])
+            power = int(np.sum(np.abs(s_t[t0:T]) ** 2))                # s(t - D) at t = t0 .. T - 1
+            want = g[i] * np.conj(g[j]) * power
+            p = o.pidx(i, j, N)
+            assert v[0, p, 0] == want.real and v[0, p, 1] == want.imag, (i, j)
+
+
+def pin_time_shift_counts_give_mask_counts(o):
+    """The shift's counters (c += d_n, x += min(d_i, d_j)), combined by the counter scheme with a
+    channel's loss counter, give the brute-force count of samples valid for both inputs."""
+    rng = np.random.default_rng(43)
+    N, F, T = 16, 8, 96
+    d = rng.integers(0, T + 1, N)
+    lost = np.zeros(F, np.uint32)
+    c, x = o.time_shift_counts(d, N, F)
+    valid = (np.arange(T)[:, None, None] >= d[None, None, :]) & np.ones((T, F, N), bool)
+    np.testing.assert_array_equal(o.counts_from_counters(T, lost, N, c, x), o.counts_from_mask(valid.astype(np.uint8)))
+    c2, x2 = o.time_shift_counts(d, N, F, c.copy(), x.copy())      # the counters add up
+    np.testing.assert_array_equal(c2, 2 * c)
+    np.testing.assert_array_equal(x2, 2 * x)
+
+
 PINS = [pin_sample_decode, pin_pidx_bijection, pin_brute_force, pin_pairs, pin_library_gram, pin_subset_channels,
         pin_autocorrelation, pin_constant_input, pin_single_source, pin_overflow_bound,
         pin_assembly_basic, pin_assembly_permutation, pin_assembly_loss_and_dups, pin_assembly_window,
         pin_assembly_random_by_definition,
         pin_counts_counters_equal_mask, pin_normalize, pin_table1_geometry, pin_flag_footer_layout,
-        pin_flag_counts_brute_force, pin_flag_counts_give_mask_counts]
+        pin_flag_counts_brute_force, pin_flag_counts_give_mask_counts,
+        pin_time_shift_brute_force, pin_time_shift_constant_input, pin_time_shift_aligns_delayed_source,
+        pin_time_shift_counts_give_mask_counts]
 
 
 @pytest.mark.parametrize("pin", PINS, ids=[p.__name__ for p in PINS])

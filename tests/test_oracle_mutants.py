@@ -55,6 +55,11 @@ MUTANTS = {
     "flags_of_duplicates": ("if (seen[(size_t)slot * G + g]) continue;", "(void)0;"),
     # footer bits read most significant first
     "flag_bit_order": ("if (!((bits[i / 8] >> (i % 8)) & 1)) continue;", "if (!((bits[i / 8] >> (7 - i % 8)) & 1)) continue;"),
+    # time shift taken towards earlier samples
+    "time_shift_direction": ("const int src = t - delays[n];", "const int src = t + delays[n] < T ? t + delays[n] : -1;"),
+    # pairs of shifted inputs share the larger delay's leading samples
+    "time_shift_counts_max": ("const int m = delays[i] < delays[j] ? delays[i] : delays[j];",
+                              "const int m = delays[i] > delays[j] ? delays[i] : delays[j];"),
     # normalisation applied as a product instead of a quotient
     "normalize_product": ("out[2 * q] = (float)((double)vis[2 * q] / (double)n[q]);",
                           "out[2 * q] = (float)((double)vis[2 * q] * (double)n[q]);"),
