@@ -131,6 +131,35 @@ int xe_assemble_noalloc(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_strid
  */
 int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *stream);
 
+/* ---------------------------------------------------------------- time shift (Fig. 4) */
+
+/*
+ * Integer time shift of every input, the "time shifting" stage Fig. 4's caption names among the
+ * optional GPU stages between a frame's transfer and its correlation (the paper defines it no
+ * further). Reading used: input n of every channel is delayed by delays[n] samples,
+ *   out[t][f][n] = in[t - delays[n]][f][n] for t >= delays[n], 0 (no data) for t < delays[n];
+ * a common signal that reaches input n tau_n samples late is re-aligned by delays[n] = D - tau_n.
+ * Lost samples of the input frame are zeros and stay zeros. Run it on an assembled frame before
+ * xe_correlate.
+ *   in, out     device, uint8 [T][F][N], distinct buffers, 16-byte aligned
+ *   delays      HOST, int32 [N], 0 <= delays[n] <= T (read during the call)
+ * Errors: XE_EINVAL (shape, pointers, overlap, alignment, a delay out of range), XE_ECUDA.
+ */
+int xe_time_shift(const uint8_t *in, xe_shape s, const int32_t *delays, uint8_t *out, void *stream);
+
+/*
+ * The shift's samples without data, as the per-input counters xe_normalize takes (Sec. II-C):
+ *   flag_count[f][n] += delays[n]                   (input n has no data in its first delays[n] samples)
+ *   flag_pairs[f][p(i,j)] += min(delays[i], delays[j])  (samples missing for both inputs)
+ * for every channel f. With these (added to any F-engine flag counts), xe_normalize divides each
+ * visibility by the number of samples in which both inputs had data.
+ *   delays      HOST, int32 [N], as for xe_time_shift
+ *   flag_count  device, uint32 [F][N], in/out;  flag_pairs  device, uint32 [F][P], in/out
+ * Errors: XE_EINVAL, XE_ECUDA.
+ */
+int xe_time_shift_counts(const int32_t *delays, xe_shape s, uint32_t *flag_count, uint32_t *flag_pairs,
+                         void *stream);
+
 /* ---------------------------------------------------------------- A3/A4: correlation */
 
 /* Engines of the correlation. */

@@ -31,7 +31,7 @@ EXPORTED = [
     "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched", "xe_tune_table_set",
     "xe_tune_table_get",
     "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_flag_counts_workspace_size",
-    "xe_flag_counts", "xe_normalize", "xe_probe_mma_legacy",
+    "xe_flag_counts", "xe_normalize", "xe_probe_mma_legacy", "xe_time_shift", "xe_time_shift_counts",
     "xe_stream_create", "xe_stream_submit", "xe_stream_submit_device", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
     "xe_stream_stats", "xe_stream_destroy",
 ]
@@ -133,6 +133,8 @@ def _load():
     L.xe_flag_counts_workspace_size.argtypes = [Shape]
     L.xe_flag_counts.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, vp, sz, vp]
     L.xe_normalize.argtypes = [vp, Shape, u32, vp, vp, vp, vp, vp, vp]
+    L.xe_time_shift.argtypes = [vp, Shape, vp, vp, vp]
+    L.xe_time_shift_counts.argtypes = [vp, Shape, vp, vp, vp]
     L.xe_stream_create.argtypes = [ctypes.POINTER(StreamCfg), ctypes.POINTER(vp)]
     L.xe_stream_submit.argtypes = [vp, i32, vp, u32]
     L.xe_stream_submit_device.argtypes = [vp, i32, vp, vp, u32]
@@ -345,6 +347,30 @@ def xe_correlate_packets(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_p
     _check(_L.xe_correlate_packets(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _dptr(vis),
                                    1 if accumulate else 0, _dptr(filled), _dptr(lost), _dptr(stats), _dptr(ws),
                                    _nbytes(ws), _stream(stream)), "xe_correlate_packets")
+
+
+# ----------------------------------------------------------------------------- time shift
+
+def _host_delays(delays, n_inputs: int):
+    import numpy as np
+
+    d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+    if d.shape != (n_inputs,):
+        raise ValueError("delays: one int32 per input")
+    return d
+
+
+def xe_time_shift(frame_in, shape: Shape, delays, frame_out, stream=None):
+    """Delays input n of every channel by delays[n] samples (host sequence of N ints)."""
+    d = _host_delays(delays, shape.n_inputs)
+    _check(_L.xe_time_shift(_dptr(frame_in), shape, d.ctypes.data, _dptr(frame_out), _stream(stream)), "xe_time_shift")
+
+
+def xe_time_shift_counts(delays, shape: Shape, flag_count, flag_pairs, stream=None):
+    """Adds the shift's samples without data to xe_normalize's per-input counters."""
+    d = _host_delays(delays, shape.n_inputs)
+    _check(_L.xe_time_shift_counts(d.ctypes.data, shape, _dptr(flag_count), _dptr(flag_pairs), _stream(stream)),
+           "xe_time_shift_counts")
 
 
 # ----------------------------------------------------------------------------- A5

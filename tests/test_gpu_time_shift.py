@@ -1,0 +1,138 @@
+"""The time-shift stage (xe_time_shift, xe_time_shift_counts) through the C ABI against the oracle
+(GPU). The shifted frame and the counters are integer work: bit-exact. End to end, packets are
+assembled, shifted, correlated and normalised on the device and compared with the same chain on the
+oracle (correlation bit-exact, normalisation within 1e-6 relative)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_1503_06189_b300 as xe
+from tests import xe_cuda as X
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-6
+
+
+def _delays(rng, N, T, uniform_blocks=0):
+    d = rng.integers(0, T + 1, N)
+    d[0], d[-1] = 0, T                                      # no shift, and nothing left
+    for b in range(uniform_blocks):                         # some blocks of 16 inputs share one delay
+        d[16 * b:16 * b + 16] = rng.integers(0, T + 1)
+    return d
+
+
+def _shift_gpu(fr, d):
+    T, F, N = fr.shape
+    src = X.dev(fr)
+    out = torch.full_like(src, 0xA5)
+    xe.xe_time_shift(src, xe.Shape(N, F, T), d, out)
+    return out
+
+
+@pytest.mark.parametrize("N,F,T,ub", [(16, 3, 37, 0), (48, 2, 300, 1), (64, 5, 1, 2), (256, 8, 4100, 8),
+                                      (272, 2, 513, 3), (1024, 1, 200, 0)])
+def test_time_shift_matches_oracle(N, F, T, ub):
+    rng = np.random.default_rng(N + T)
+    fr = synth.uniform_frame(N, F, T, 3 * N + T)
+    d = _delays(rng, N, T, ub)
+    got = _shift_gpu(fr, d).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.time_shift(fr, d))
+
+
+def test_time_shift_zero_delays_and_empty_frame():
+    fr = synth.uniform_frame(32, 2, 64, 9)
+    np.testing.assert_array_equal(_shift_gpu(fr, np.zeros(32, int)).cpu().numpy(), fr)
+    a = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    b = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    xe.xe_time_shift(a, xe.Shape(32, 2, 0), np.zeros(32, int), b)           # T = 0: nothing to do
+
+
+def test_time_shift_counts_match_oracle():
+    rng = np.random.default_rng(5)
+    N, F, T = 80, 3, 1000
+    d = _delays(rng, N, T, 2)
+    c0 = rng.integers(0, 50, (F, N)).astype(np.uint32)
+    x0 = rng.integers(0, 50, (F, xe.npairs(N))).astype(np.uint32)
+    c = X.dev(c0.view(np.int32))
+    x = X.dev(x0.view(np.int32))
+    xe.xe_time_shift_counts(d, xe.Shape(N, F, T), c, x)
+    wc, wx = oracle.time_shift_counts(d, N, F, c0.copy(), x0.copy())
+    np.testing.assert_array_equal(c.cpu().numpy().view(np.uint32), wc)
+    np.testing.assert_array_equal(x.cpu().numpy().view(np.uint32), wx)
+
+
+def test_time_shift_rejects_bad_arguments():
+    N, F, T = 32, 2, 64
+    s = xe.Shape(N, F, T)
+    a = torch.zeros((T, F, N), dtype=torch.uint8, device="cuda")
+    b = torch.zeros_like(a)
+    for bad in (np.full(N, T + 1), np.full(N, -1)):
+        with pytest.raises(xe.XeError):
+            xe.xe_time_shift(a, s, bad, b)
+    with pytest.raises(xe.XeError):                           # in place is not supported
+        xe.xe_time_shift(a, s, np.zeros(N, int), a)
+    with pytest.raises(ValueError):                           # one delay per input
+        xe.xe_time_shift(a, s, np.zeros(N - 1, int), b)
+
+
+def test_time_shift_realigns_delayed_source():
+    """A common source reaching input n tau_n samples late, re-aligned by delays D - tau_n: the
+    correlation equals g_i conj(g_j) times the source power over the samples both inputs keep."""
+    rng = np.random.default_rng(7)
+    N, T, D = 64, 2048, 100
+    tau = rng.integers(0, D + 1, N)
+    tau[0] = D
+    g = rng.integers(-1, 2, N) + 1j * rng.integers(-1, 2, N)
+    s_t = rng.integers(-3, 4, T + D) + 1j * rng.integers(-3, 4, T + D)
+    x = np.stack([g[n] * s_t[D - tau[n]:D - tau[n] + T] for n in range(N)], axis=1)
+    fr = synth.pack(x.real.astype(np.int64), x.imag.astype(np.int64))[:, None, :]
+    d = D - tau
+    vis = X.correlate(_shift_gpu(fr, d)).cpu().numpy().astype(np.int64)
+    mag2 = (s_t.real.astype(np.int64) ** 2 + s_t.imag.astype(np.int64) ** 2)[:T]   # |s(t - D)|^2 at t = 0 .. T - 1
+    power = np.cumsum(mag2[::-1])[::-1]                                            # power[t0] = sum over t >= t0
+    for i in range(0, N, 7):
+        for j in range(i, N, 5):
+            want = g[i] * np.conj(g[j]) * power[max(d[i], d[j])]
+            p = oracle.pidx(i, j, N)
+            assert vis[0, p, 0] == want.real and vis[0, p, 1] == want.imag, (i, j)
+
+
+def test_time_shift_in_the_frame_pipeline():
+    """Packets (with loss and reordering) -> xe_assemble -> xe_time_shift -> xe_correlate ->
+    xe_time_shift_counts + xe_normalize, against the same chain on the oracle."""
+    rng = np.random.default_rng(11)
+    N, F, T, gps = 256, 16, 2048, 1
+    s = xe.Shape(N, F, T)
+    fr = synth.signal_frame(N, F, T, 12)
+    pk = synth.packet_stream(fr, 0, gps, seed=13, p_drop=0.01, p_reorder=0.05, p_dup=0.01)
+    d = _delays(rng, N, 300, 4)
+    frame = torch.empty((T, F, N), dtype=torch.uint8, device="cuda")
+    shifted = torch.empty_like(frame)
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device="cuda")
+    lost = torch.zeros(F, dtype=torch.int32, device="cuda")
+    stats = torch.zeros(5, dtype=torch.int32, device="cuda")
+    ws = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device="cuda")
+    xe.xe_assemble(X.dev(pk), pk.shape[0], pk.shape[1], 0, gps, s, frame, filled, lost, stats, ws)
+    xe.xe_time_shift(frame, s, d, shifted)
+    vis = X.correlate(shifted)
+    c = torch.zeros((F, N), dtype=torch.int32, device="cuda")
+    x = torch.zeros((F, xe.npairs(N)), dtype=torch.int32, device="cuda")
+    xe.xe_time_shift_counts(d, s, c, x)
+    out = torch.empty((F, xe.npairs(N), 2), dtype=torch.float32, device="cuda")
+    n_out = torch.empty((F, xe.npairs(N)), dtype=torch.int32, device="cuda")
+    xe.xe_normalize(vis, s, T, lost, out, n_out, flag_count=c, flag_pairs=x)
+    torch.cuda.synchronize()
+
+    fo, _, lost_o, _ = oracle.assemble(pk, 0, gps, N, F, T)
+    want, st = oracle.correlate(oracle.time_shift(fo, d))
+    assert st == oracle.OK
+    np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want)
+    co, xo = oracle.time_shift_counts(d, N, F)
+    n = oracle.counts_from_counters(T, lost_o, N, co, xo)
+    np.testing.assert_array_equal(n_out.cpu().numpy().view(np.uint32), n)
+    ref = oracle.normalize(want, n)
+    o = out.cpu().numpy()
+    assert np.all(np.abs(o - ref) <= REL_TOL * np.abs(ref))

@@ -495,7 +495,8 @@ def pin_time_shift_aligns_delayed_source(o):
     for i in range(N):
         for j in range(i, N):
             t0 = max(d[i], d[j])
-            power = int(np.sum(np.abs(s_t[t0:T]) ** 2))                # s(t - D) at t = t0 .. T - 1
+            seg = s_t[t0:T]                                             # s(t - D) at t = t0 .. T - 1
+            power = int(np.sum(seg.real.astype(np.int64) ** 2 + seg.imag.astype(np.int64) ** 2))
             want = g[i] * np.conj(g[j]) * power
             p = o.pidx(i, j, N)
             assert v[0, p, 0] == want.real and v[0, p, 1] == want.imag, (i, j)
