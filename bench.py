@@ -750,14 +750,30 @@ def run_config_reference(args):
                       + f" ({dt:.1f} s of CPU work)", "seconds": dt}
 
 
-def useful_mma_fraction(shapes):
-    """Useful real MACs (4 per CMAC) over the MMA work the frame-mode pair engine issues (whole
-    256 x 256 blocks of the 2N-row Gram matrix on or above the block diagonal)."""
+def block_products(N, layout):
+    """256 x 256 block products per sample and channel that the pair engine issues for N inputs:
+    every Gram block on or above the block diagonal, or with the fold layout two per whole
+    256-input super-block plus the Gram blocks outside the super-blocks."""
+    import paper_1503_06189_b300 as xe
+
+    nb = -(-2 * N // 256)
+    fold = nb >= 2 and layout in (xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_FOLD)
+    if not fold:
+        return nb * (nb + 1) // 2
+    return 2 * (nb // 2) + (nb & 1) + sum(max(0, nb - 2 * (r // 2 + 1)) for r in range(nb))
+
+
+def useful_mma_fraction(shapes, layouts=None):
+    """Useful real MACs (4 per CMAC) over the MMA work the pair engine issues (block_products per
+    job; `layouts` per job, default: whole Gram blocks). Above 1 where the fold layout's two
+    products cover a super-block's Hermitian square."""
+    import paper_1503_06189_b300 as xe
+
     useful = issued = 0
-    for N, F, T in shapes:
-        nb = -(-2 * N // 256)
+    for k, (N, F, T) in enumerate(shapes):
+        lay = layouts[k] if layouts else xe.XE_LAYOUT_FRAME_BLOCKS
         useful += 4 * npairs(N) * F * T
-        issued += nb * (nb + 1) // 2 * 256 * 256 * F * T
+        issued += block_products(N, lay) * 256 * 256 * F * T
     return useful / issued
 
 
@@ -787,16 +803,22 @@ def run_config(args):
     jobs = [(fr, v, xe.Shape(*sh), False) for fr, v, sh in zip(frames, vis, shapes)]
     ws = torch.empty(xe.xe_correlate_batched_workspace_size(jobs), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(device=dev)
-    # configuration 4: the autotuner picks the pair engine's launch shape per (N, T-bucket) of the jobs
-    tuning = None
-    if cfg == 4:
-        from paper_1503_06189_b300 import autotune
-        table = autotune.Table(None)
-        for N, F, T in shapes:
-            table.tune_frames(N, T)
-        table.install()
-        tuning = [{k: e[k] for k in ("n_inputs", "t_bucket", "mode", "pairs", "odd_pairs", "ms")}
-                  for e in table.entries.values()]
+    # the autotuner picks the pair engine's kernel, layout and launch shape per (N, T-bucket) of the jobs
+    from paper_1503_06189_b300 import autotune
+    table = autotune.Table(None)
+    for N, F, T in shapes:
+        table.tune_frames(N, T)
+    table.install()
+    tuning = [{k: e[k] for k in ("n_inputs", "t_bucket", "mode", "layout", "pairs", "odd_pairs", "ms")}
+              for e in table.entries.values()]
+    # the layout each job runs: the largest job's entry picks the kernel for the whole launch
+    layouts = [table.entries[autotune.key("frames", N, T)]["layout"] for N, F, T in shapes]
+    big_n, _, big_t = max(shapes, key=lambda sh: sh[1] * npairs(sh[0]) * sh[2])
+    if any(T % 4 for N, F, T in shapes) or \
+            table.entries[autotune.key("frames", big_n, big_t)]["layout"] == xe.XE_LAYOUT_FRAME_BLOCKS:
+        layouts = [xe.XE_LAYOUT_FRAME_BLOCKS] * len(shapes)      # the 256-sample kernel
+    else:
+        layouts = [xe.XE_LAYOUT_AUTO if lay == xe.XE_LAYOUT_FRAME_BLOCKS else lay for lay in layouts]
     reps = {1: 2000, 2: 20, 4: 1, 6: 2}[cfg]           # launches per step: a step lasts >= ~10 ms
     cmac_step = reps * sum(F * npairs(N) * T for N, F, T in shapes)
     n_ev = reps * max(args.steps, 1)
@@ -893,17 +915,14 @@ def run_config(args):
                    "l2": "256 MiB written between steps" + ("; the tiny frame itself fits in L2" if cfg == 1 else "")},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
-                     "useful_mma_fraction": useful_mma_fraction(shapes),
+                     "useful_mma_fraction": useful_mma_fraction(shapes, layouts),
                      "kernel": "xe_correlate_batched (CTA-pair tcgen05 correlation), 8 int ops per CMAC",
                      "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
         "gpu_launches": args.steps * reps * (1 + len(shapes)),
         "clocks": clocks, "e2e": e2e,
     }
-    if cfg == 4:
-        line["tuning"] = tuning
-        line["graph_ms_per_step"] = graph_ms
-    else:
-        line["graph_ms_per_step"] = graph_ms
+    line["tuning"] = tuning
+    line["graph_ms_per_step"] = graph_ms
     if sky:
         line["realtime_factor"] = cmac_step / (ms / 1e3) / (npairs(shapes[0][0]) * shapes[0][1] * SAMPLE_RATE)
     base = run_config_reference(args)

@@ -143,6 +143,9 @@ int xe_unpack(const uint8_t *frame, xe_shape s, uint8_t *y, int64_t ldy, void *s
  * xe_correlate.
  *   in, out     device, uint8 [T][F][N], distinct buffers, 16-byte aligned
  *   delays      HOST, int32 [N], 0 <= delays[n] <= T (read during the call)
+ * When the delays of every 128 consecutive inputs lie within 256 samples of each other, tiles of
+ * 128 rows x 128 inputs are shifted through shared memory (bounded device waits: XE_ETIMEOUT in
+ * xe_device_status); wider spreads take a kernel that reads each sample from global memory.
  * Errors: XE_EINVAL (shape, pointers, overlap, alignment, a delay out of range), XE_ECUDA.
  */
 int xe_time_shift(const uint8_t *in, xe_shape s, const int32_t *delays, uint8_t *out, void *stream);
@@ -215,12 +218,18 @@ int xe_probe_mma_legacy(int32_t kind, int32_t blocks, int32_t iters, int32_t *si
 
 /* ---------------------------------------------------------------- tuning table (A6) */
 
-/* Item layouts of the CTA-pair engine in packet mode (xe_correlate_packets, the serving loop). */
+/* Item layouts of the CTA-pair engine. Packet mode (xe_correlate_packets, the serving loop) runs a
+ * kernel with 128-sample stages that reads samples in 4-sample slots, with layouts 0-4. Frame mode
+ * (xe_correlate, xe_correlate_batched) runs either that kernel (T % 4 == 0 only) or a kernel with
+ * 256-sample stages and every Gram block its own item (XE_LAYOUT_FRAME_BLOCKS). Without a table
+ * entry a frame launch takes the 128-sample kernel with the fold layout when its largest job has
+ * 129 to 256 inputs, and the 256-sample kernel otherwise. */
 #define XE_LAYOUT_AUTO 0       /* fold for N > 128; below, Gram blocks with twins from T >= 16384 */
 #define XE_LAYOUT_GRAM 1       /* Gram blocks: doubles and singles, twins from T >= 16384, wide singles below */
 #define XE_LAYOUT_GRAM_TWIN 2  /* Gram blocks, twins at any T */
 #define XE_LAYOUT_GRAM_WIDE 3  /* Gram blocks, wide singles at any T */
 #define XE_LAYOUT_FOLD 4       /* one fold item per whole 256-input super-block (N > 128; else GRAM) */
+#define XE_LAYOUT_FRAME_BLOCKS 5   /* frame mode: every Gram block its own item, 256-sample stages */
 
 /*
  * One entry of the library's tuning table: the choices of the CTA-pair engine for jobs with N inputs
@@ -228,7 +237,8 @@ int xe_probe_mma_legacy(int32_t kind, int32_t blocks, int32_t iters, int32_t *si
  * frames). The table is filled by an
  * autotuner that measures the candidates on the device (paper_1503_06189_b300/autotune.py) and is
  * consulted by every pair-engine launch: a batched launch takes each job's layout from its own
- * entry, and the launch-wide choices (pairs, odd_pairs, k_flush) from the entry of its largest job.
+ * entry, and the launch-wide choices (pairs, odd_pairs, k_flush, and in frame mode the kernel:
+ * XE_LAYOUT_FRAME_BLOCKS or not) from the entry of its largest job.
  * A non-zero field of an explicit xe_tune argument overrides the table.
  */
 #define XE_TUNE_PACKETS 0      /* entry for packet-mode launches (xe_correlate_packets, serving loop) */
@@ -238,7 +248,7 @@ typedef struct {
     int32_t n_inputs;   /* N of the entry */
     int32_t t_bucket;   /* T bucket: power of two >= 128 */
     int32_t mode;       /* XE_TUNE_PACKETS or XE_TUNE_FRAMES */
-    int32_t layout;     /* XE_LAYOUT_* (packet mode; frame mode: XE_LAYOUT_AUTO) */
+    int32_t layout;     /* XE_LAYOUT_* (XE_LAYOUT_FRAME_BLOCKS: frame mode only) */
     int32_t pairs;      /* CTA pairs per launch, 0 = as many as can be resident */
     int32_t odd_pairs;  /* 1: an odd pair count, 0: as counted, -1: the layout's default (odd for Gram) */
     int32_t k_flush;    /* drain interval in samples, multiple of 128 up to 32768; 0 = default */

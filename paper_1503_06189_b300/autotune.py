@@ -4,8 +4,10 @@
 - packet mode (xe_correlate_packets and the serving loop): the work-item layout -- fold items over
   whole 256-input super-blocks, Gram blocks with twins, or Gram blocks with wide singles -- and
   whether the launch takes an odd number of CTA pairs;
-- frame mode (xe_correlate, xe_correlate_batched): the number of CTA pairs (fewer pairs can end a
-  launch's last round of work items more evenly) and its parity.
+- frame mode (xe_correlate, xe_correlate_batched): the kernel and layout -- the 128-sample kernel
+  (the packet-mode kernel reading the frame in 4-sample slots) with any of those layouts, or the
+  256-sample frame kernel with every Gram block its own item -- the number of CTA pairs (fewer
+  pairs can end a launch's last round of work items more evenly) and its parity.
 
 Each candidate runs on seeded random samples of the bucket's shape on the device (F chosen so that
 a launch has about four rounds of work items, within a few GB), timed with CUDA events (best of
@@ -44,11 +46,11 @@ def blocks(n_inputs: int) -> int:
     return -(-2 * int(n_inputs) // 256)
 
 
-def items_per_channel(n_inputs: int, layout: int, n_time: int, packets: bool = True) -> float:
+def items_per_channel(n_inputs: int, layout: int, n_time: int) -> float:
     """Work items of one channel (the library's layouts; a twin counts half for each of its two
     channels)."""
     nb = blocks(n_inputs)
-    if not packets:
+    if layout == xe.XE_LAYOUT_FRAME_BLOCKS:
         return nb * (nb + 1) / 2
     fold = nb >= 2 and layout in (xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_FOLD)
     if fold:
@@ -59,23 +61,33 @@ def items_per_channel(n_inputs: int, layout: int, n_time: int, packets: bool = T
     return per_ch + (0.5 if twin else 1.0)
 
 
+def row_layouts(n_inputs: int) -> list[int]:
+    """Layouts of the 128-sample kernel worth measuring: fold or Gram blocks above 128 inputs, twins
+    or wide singles for a single block."""
+    return [xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM] if blocks(n_inputs) >= 2 else \
+        [xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE]
+
+
 def packet_candidates(n_inputs: int) -> list[dict]:
     """Layouts worth measuring in packet mode, each with and without an odd pair count."""
-    layouts = [xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM] if blocks(n_inputs) >= 2 else \
-        [xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE]
-    return [dict(layout=lay, pairs=0, odd_pairs=odd, k_flush=0) for lay in layouts for odd in (0, 1)]
+    return [dict(layout=lay, pairs=0, odd_pairs=odd, k_flush=0) for lay in row_layouts(n_inputs) for odd in (0, 1)]
 
 
-def frame_candidates(n_inputs: int, n_chan: int) -> list[dict]:
-    """Pair counts worth measuring in frame mode: all, an odd count, and the smallest count that
-    keeps the number of rounds of work items (fewer pairs finish a ragged last round together)."""
-    items = int(items_per_channel(n_inputs, xe.XE_LAYOUT_AUTO, 0, packets=False)) * n_chan
+def frame_candidates(n_inputs: int, n_chan: int, n_time: int = 4096) -> list[dict]:
+    """Frame mode: the 128-sample kernel's layouts with and without an odd pair count (whole 4-sample
+    slots only), and the 256-sample kernel with all pairs, an odd count, and the smallest count that
+    keeps its number of rounds of work items (fewer pairs finish a ragged last round together)."""
+    cands = []
+    if n_time % 4 == 0:
+        cands = [dict(layout=lay, pairs=0, odd_pairs=odd, k_flush=0) for lay in row_layouts(n_inputs)
+                 for odd in (0, 1)]
+    items = int(items_per_channel(n_inputs, xe.XE_LAYOUT_FRAME_BLOCKS, n_time)) * n_chan
     rounds = -(-items // PAIRS)
     even = -(-items // rounds)
-    cands = [dict(layout=xe.XE_LAYOUT_AUTO, pairs=0, odd_pairs=0, k_flush=0),
-             dict(layout=xe.XE_LAYOUT_AUTO, pairs=0, odd_pairs=1, k_flush=0)]
+    blk = dict(layout=xe.XE_LAYOUT_FRAME_BLOCKS, pairs=0, k_flush=0)
+    cands += [dict(blk, odd_pairs=0), dict(blk, odd_pairs=1)]
     if even < PAIRS:
-        cands.append(dict(layout=xe.XE_LAYOUT_AUTO, pairs=even, odd_pairs=0, k_flush=0))
+        cands.append(dict(blk, pairs=even, odd_pairs=0))
     return cands
 
 
@@ -140,8 +152,8 @@ def measure_frames(n_inputs: int, n_time: int, candidates=None, reps: int = 3) -
     import synth
 
     T = bucket(n_time)
-    F = probe_chan(n_inputs, T, items_per_channel(n_inputs, xe.XE_LAYOUT_AUTO, T, packets=False), 1)
-    cands = candidates or frame_candidates(n_inputs, F)
+    F = probe_chan(n_inputs, T, items_per_channel(n_inputs, xe.XE_LAYOUT_AUTO, T), 1)    # fewest items
+    cands = candidates or frame_candidates(n_inputs, F, T)
     dev = torch.device("cuda", torch.cuda.current_device())
     frame = synth.uniform_frame_torch(n_inputs, F, T, n_inputs * 137 + T, device=dev)
     vis = torch.zeros((F, xe.npairs(n_inputs), 2), dtype=torch.int32, device=dev)

@@ -85,6 +85,7 @@ struct Params {
     int32_t wide_diag;            // 1: single diagonal items run in wide stages (packet mode)
     int32_t op_stages, pk_stages, slots, n_acc;
     int32_t fold;                 // some job has the fold layout: three operand slots, transpose staging
+    int32_t frame_rows;           // 128-sample kernel reading assembled frames (no owner tables)
     int *status;
     int *counter;            // work-item counter, zero at launch
     uint64_t limit_ns;
@@ -860,8 +861,10 @@ struct PairLoader {
     bool wide;                                // packet mode: a wide stage (B rows = the next kKt samples)
     const uint8_t *pa, *pb;                   // frame: sample kt * S::kKt + t_row; packets: in packet 0
     int64_t step, rstep;                      // frame: bytes per stage / between a thread's rows
-    const uint32_t *own;                      // packets: owner entry of slot kt * S::kKt / 4 + lane
-    int s_left;                               // packets: T / 4 - (kt * S::kKt / 4 + lane)
+    // packets: address of the owner entry of slot kt * S::kKt / 4 + lane; frame rows in the
+    // 128-sample kernel (no owner table): 4 x that slot, which is then the "packet" itself
+    uintptr_t own;
+    int s_left;                               // T / 4 - (kt * S::kKt / 4 + lane)
     int64_t pstride;
 
     __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
@@ -891,10 +894,18 @@ struct PairLoader {
         const uint8_t *base;
         if constexpr (kPackets) {
             const int Q = jb.n_time / 4, lane = threadIdx.x & 31;
-            base = jb.pkts + 16 + ((size_t)(t_row & 3) * 8 + it.f % 8) * N;
-            own = jb.owner + (size_t)(it.f / 8) * Q + lane;
+            if (!p.frame_rows) {
+                base = jb.pkts + 16 + ((size_t)(t_row & 3) * 8 + it.f % 8) * N;
+                own = reinterpret_cast<uintptr_t>(jb.owner + (size_t)(it.f / 8) * Q + lane);
+                pstride = jb.pkt_stride;
+            } else {
+                // an assembled frame read in the same 4-sample slots: slot s stands for a packet
+                // whose rows 4 s .. 4 s + 3 lie 4 F N bytes on from those of slot s - 1
+                base = jb.frame + ((size_t)(t_row & 3) * F + it.f) * N;
+                own = (uintptr_t)lane * 4;
+                pstride = (int64_t)4 * F * N;
+            }
             s_left = Q - lane;
-            pstride = jb.pkt_stride;
         } else {
             base = jb.frame + ((size_t)t_row * F + it.f) * N;
             step = (int64_t)S::kKt * F * N;
@@ -911,7 +922,7 @@ struct PairLoader {
     __device__ __forceinline__ void next(const Params &p, int n_pairs, uint32_t rank, int t_row, int c) {
         t_left -= S::kKt;
         if constexpr (kPackets) {
-            own += (wide ? 2 : 1) * (S::kKt / 4);
+            own += (wide ? 2 : 1) * S::kKt;       // kKt / 4 slots of 4 bytes
             s_left -= (wide ? 2 : 1) * (S::kKt / 4);
         } else {
             pa += step;
@@ -923,13 +934,15 @@ struct PairLoader {
     }
     // packets: the packets of slots lane, lane + 32, ... of the current stage (a wide stage: then
     // those of slots kKt / 4 + lane, ... in o[kOwn ..])
-    __device__ __forceinline__ void owners(uint32_t (&o)[kOwnMax]) const {
+    __device__ __forceinline__ void owners(const Params &p, uint32_t (&o)[kOwnMax]) const {
 #pragma unroll
         for (int q = 0; q < kOwnMax; ++q) {
             o[q] = kNoPacket;
             if constexpr (kPackets) {
-                if ((q < kOwn || wide) && s_left > 32 * q)
-                    asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[q]) : "l"(own + 32 * q));
+                if ((q < kOwn || wide) && s_left > 32 * q) {
+                    if (!p.frame_rows) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[q]) : "l"(own + 128 * q));
+                    else o[q] = (uint32_t)(own / 4) + 32 * q;           // frame rows: the slot itself
+                }
             }
         }
     }
@@ -1214,34 +1227,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 const int base = 256 * it.R;
                 const uint32_t tb = tmem + (uint32_t(q * 32) << 16);
                 auto prow_of = [N](int r) -> int32_t { return r * N - r * (r - 1) / 2 - r; };
-                // 16 visibilities (one half of a 32-column TMEM chunk): elem(c, pos, dij, dji) gives element
-                // c's position in the triangle, D[i][j] and D[j][i], and whether it is written. The old
-                // values (when adding) are all loaded first (sixteen loads in flight per thread) and through
-                // L2 only: cached in L1 they were an order of magnitude slower here.
-                auto chunk16 = [&](auto elem, bool add) {
-                    int2 o[16];
+                const int j = base + 128 * (int)rank + m;            // this thread's row of D
+                // 16 visibilities V[ii0 + c][j], c < n_ok (one half of a 32-column TMEM chunk), from
+                // D[ii0 + c][j] = stg[c][m] (staging rows r0 + c, whose swizzle phase is c & 7 as r0 is
+                // a multiple of 16) and D[j][ii0 + c] = h16[c]. Positions advance row by row: V[ii + 1][j]
+                // lies N - ii - 1 entries after V[ii][j]. Adding to existing values is left to L2
+                // (red.add of Re and Im): the thread waits for no load, where loading the old values kept
+                // the epilogue bound by their latency. Each visibility has one writer thread in every
+                // drain, so the integer sums are exact and independent of order.
+                auto chunk16 = [&](int ii0, const float *stg, int n_ok, const uint32_t (&h)[16], bool add) {
+                    int32_t pos = prow_of(ii0) + j;
+                    const int32_t step0 = N - ii0 - 1;
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
-                        int32_t pos;
-                        float a, b;
-                        const bool v = elem(c, pos, a, b);
-                        o[c] = add && v ? __ldcg(reinterpret_cast<const int2 *>(vis_f) + pos) : make_int2(0, 0);
-                    }
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        int32_t pos;
-                        float a, b;
-                        if (!elem(c, pos, a, b)) continue;
-                        const int re = __float_as_int(fmaf(a + b, 0.03125f, kMagic)) - kMagicBits;
-                        const int im = __float_as_int(fmaf(a - b, 0.03125f, kMagic)) - kMagicBits;
-                        __stcg(reinterpret_cast<int2 *>(vis_f) + pos, make_int2(re + o[c].x, im + o[c].y));
+                        if (c < n_ok) {
+                            const float a = stg[c * 128 + (m ^ (4 * (c & 7)))];
+                            const float b = __uint_as_float(h[c]);
+                            const int re = __float_as_int(fmaf(a + b, 0.03125f, kMagic)) - kMagicBits;
+                            const int im = __float_as_int(fmaf(a - b, 0.03125f, kMagic)) - kMagicBits;
+                            int32_t *v = vis_f + 2 * pos;
+                            if (add) {
+                                dev::red_add(v, re);
+                                dev::red_add(v + 1, im);
+                            } else {
+                                __stcg(reinterpret_cast<int2 *>(v), make_int2(re, im));
+                            }
+                        }
+                        pos += step0 - c;
                     }
                 };
                 // word offset of (row, col) in a [32][128] staging tile
                 auto off = [](int row, int col) -> int {
                     return row * 128 + ((((col >> 2) ^ row) & 7) | ((col >> 2) & ~7)) * 4 + (col & 3);
                 };
-                const int j = base + 128 * (int)rank + m;            // this thread's row of D
                 if (jb.accumulate) {
                     // the old values this item adds to go into L2 while its MMAs run: this warp writes
                     // columns c0 .. c0 + 31 of rows base .. c0 + 31 (CTA 0: its quadrant; CTA 1: the
@@ -1308,13 +1326,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                             for (int h = 0; h < 2; ++h) {
                                 dev::tmem_ld_32x32b_x16(ta + qcol + 32 * st + 16 * h, h16);
                                 dev::tmem_ld_wait();
-                                chunk16([&](int c, int32_t &pos, float &dij, float &dji) -> bool {
-                                    const int r = 16 * h + c, il = 32 * st + r, ii = base + 128 * (int)rank + il;
-                                    pos = prow_of(ii) + j;
-                                    dij = stage_df[off(r, m)];
-                                    dji = __uint_as_float(h16[c]);
-                                    return il <= m && j_ok;
-                                }, add);
+                                const int il0 = 32 * st + 16 * h;      // rows il0 + c <= m of the quadrant
+                                chunk16(base + 128 * (int)rank + il0, stage_df + 16 * h * 128,
+                                        j_ok ? min(16, max(0, m - il0 + 1)) : 0, h16, add);
                             }
                         }
                         if (rank == 1) {
@@ -1327,13 +1341,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                                 for (int h = 0; h < 2; ++h) {
                                     dev::tmem_ld_32x32b_x16(ta + 32 * st + 16 * h, h16);
                                     dev::tmem_ld_wait();
-                                    chunk16([&](int c, int32_t &pos, float &dij, float &dji) -> bool {
-                                        const int r = 16 * h + c, ii = base + 32 * st + r;
-                                        pos = prow_of(ii) + j;
-                                        dij = stage_xf[off(r, m)];
-                                        dji = __uint_as_float(h16[c]);
-                                        return j_ok;
-                                    }, add);
+                                    chunk16(base + 32 * st + 16 * h, stage_xf + 16 * h * 128, j_ok ? 16 : 0, h16, add);
                                 }
                             }
                             asm volatile("fence.acq_rel.cluster;" ::: "memory");   // the reads above, then the arrival
@@ -1395,7 +1403,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 }
                 // frame mode reads the next chunk's old values after this chunk's store (a look-ahead
                 // buffer would cost its 80-register converter warps); packet mode, whose epilogue drains
-                // both halves of a double item, reads them ahead
+                // both halves of a double item, reads them ahead. (Adding through red.add in L2, as the
+                // fold epilogue does, measured slower here: each warp instruction of this layout touches
+                // 32 rows of the triangle.)
 #pragma unroll 1
                 for (; ck < n_chunks; ck += kPerQuarter) {
                     const bool more = ck + kPerQuarter < n_chunks;
@@ -1467,7 +1477,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         auto next_owners = [&](Buf &b) {
             if constexpr (kPackets) {
                 if (!ow.valid(p)) return;
-                ow.owners(b.own);
+                ow.owners(p, b.own);
                 ow.next(p, n_pairs, rank, t_row, c);
             }
         };
@@ -1506,7 +1516,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             for (int q = 0; q < kOwn; ++q) nown[q] = lb.own[q];
             if constexpr (kPackets) {
                 if (ow.valid(p)) {
-                    ow.owners(nown);
+                    ow.owners(p, nown);
                     ow.next(p, n_pairs, rank, t_row, c);
                 }
             }
@@ -1792,6 +1802,27 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         if (!(tune_in && tune_in->k_flush) && launch_ent.k_flush) tune.k_flush = launch_ent.k_flush;
         if (!(tune_in && tune_in->n_ctas) && launch_ent.pairs) tune.n_ctas = 2 * launch_ent.pairs;
     }
+    // The pair engine's 128-sample kernel (the packet-mode kernel) also reads assembled frames, in
+    // 4-sample slots (whole slots only: T % 4 == 0), with every item layout. A frame launch takes it
+    // when the table's entry of its largest job names one of its layouts; without an entry, when
+    // that job has 129 to 256 inputs (one fold item per channel: measured 0.20 against 0.22 ms for
+    // 64 channels of T = 16384, where at N = 1024 or 2048 the off-diagonal blocks' conversions make
+    // it 1.6-1.9 times slower than the 256-sample kernel)
+    bool rows128 = pk != nullptr;
+    if (!pk && engine == kFusedPair) {
+        if (has_launch_ent) {
+            rows128 = launch_ent.layout != XE_LAYOUT_FRAME_BLOCKS;
+        } else {
+            int big = 0;
+            double best = -1.0;
+            for (int j = 0; j < n_jobs; ++j) {
+                const double w = (double)jobs[j].s.n_chan * (double)npairs(jobs[j].s.n_inputs) * (double)jobs[j].s.n_time;
+                if (w > best) { best = w; big = j; }
+            }
+            rows128 = jobs[big].s.n_inputs > 128 && jobs[big].s.n_inputs <= 256;
+        }
+        for (int j = 0; j < n_jobs; ++j) rows128 = rows128 && jobs[j].s.n_time % 4 == 0;
+    }
 
     static Params hp;    // large; built under a lock
     static std::mutex mu;
@@ -1819,11 +1850,18 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             d.pkt_stride = pk[j].pkt_stride;
             d.pw = 64;
             enc = XE_OK;
+        } else if (rows128) {                   // frame rows through the 128-sample kernel
+            hp.frame_rows = 1;
+            d.pkts = nullptr;
+            d.owner = nullptr;
+            d.pkt_stride = 0;
+            d.pw = 64;
+            enc = XE_OK;
         } else if (engine == kFusedMN || engine == kFusedPair) {
             const uint32_t pw = (uint32_t)std::min(64, s.n_inputs);
             const uint64_t dims[3] = {(uint64_t)s.n_inputs, (uint64_t)s.n_chan, (uint64_t)s.n_time};
             const uint64_t strides[2] = {(uint64_t)s.n_inputs, (uint64_t)s.n_inputs * s.n_chan};
-            const uint32_t box[3] = {pw, 1, (uint32_t)kt_of(engine, pk != nullptr)};
+            const uint32_t box[3] = {pw, 1, (uint32_t)kt_of(engine)};
             enc = encode_tiled(&d.tmap, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(jobs[j].frame), dims,
                                strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
             d.pw = (int)pw;
@@ -1855,8 +1893,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         if (engine == kFusedPair) {             // 256x256 blocks on or above the diagonal
             d.nb = (g.nb + 1) / 2;
             d.fold = 0;
-            const int layout = has_ent[j] ? ent[j].layout : XE_LAYOUT_AUTO;
-            if (pk && d.nb >= 2 && (layout == XE_LAYOUT_AUTO || layout == XE_LAYOUT_FOLD)) {
+            int layout = has_ent[j] ? ent[j].layout : XE_LAYOUT_AUTO;
+            if (layout == XE_LAYOUT_FRAME_BLOCKS) layout = XE_LAYOUT_AUTO;   // a job in a 128-sample launch
+            if (rows128 && d.nb >= 2 && (layout == XE_LAYOUT_AUTO || layout == XE_LAYOUT_FOLD)) {
                 // fold layout: per channel S2 / 2 fold items, a Gram diagonal single for an odd last
                 // block, and the Gram blocks (R, C) between different super-blocks (R / 2 < C / 2)
                 d.fold = 1;
@@ -1867,7 +1906,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
                 for (int r = 0; r < d.nb; ++r) per_ch += std::max(0, d.nb - 2 * (r / 2 + 1));
                 d.strips = per_ch;
                 job_items = (int64_t)d.strips * s.n_chan;
-            } else if (pk) {
+            } else if (rows128) {
                 // per channel S2 - 1 doubles and (S2 - 1)(S2 - 2) / 2 singles; then long
                 // integrations take the last diagonal blocks of channel pairs as twins (an odd last
                 // channel keeps its diagonal single), short ones each channel's as a wide single
@@ -1899,10 +1938,10 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             d.strips = strips_per_channel(g.nb, d.max_strip);
             job_items = (int64_t)d.strips * s.n_chan;
         }
-        d.k_tiles = (int)((s.n_time + kt_of(engine, pk != nullptr) - 1) / kt_of(engine, pk != nullptr));
-        // packet mode: single diagonal blocks run in stages of twice the samples
-        const int kt_wide = 2 * kt_of(engine, pk != nullptr);
-        d.k_tiles_wide = engine == kFusedPair && pk ? (int)((s.n_time + kt_wide - 1) / kt_wide) : d.k_tiles;
+        d.k_tiles = (int)((s.n_time + kt_of(engine, rows128) - 1) / kt_of(engine, rows128));
+        // 128-sample kernel: single diagonal blocks run in stages of twice the samples
+        const int kt_wide = 2 * kt_of(engine, rows128);
+        d.k_tiles_wide = engine == kFusedPair && rows128 ? (int)((s.n_time + kt_wide - 1) / kt_wide) : d.k_tiles;
         d.item_begin = items;
         if (items + job_items > INT32_MAX / 2) return XE_EINVAL;
         items += (int)job_items;
@@ -1911,9 +1950,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     hp.n_jobs = nj;
     hp.n_items = items;
     // drain at least once per stage; a stage (<= 256 samples) never exceeds the exactness bound
-    hp.k_flush_tiles = std::max(1, tune.k_flush / kt_of(engine, pk != nullptr));
+    hp.k_flush_tiles = std::max(1, tune.k_flush / kt_of(engine, rows128));
     // wide stages (2 x 128 samples) stay within the exactness bound like any stage of <= 256 samples
-    hp.wide_diag = engine == kFusedPair && pk ? 1 : 0;
+    hp.wide_diag = engine == kFusedPair && rows128 ? 1 : 0;
     hp.k_flush_tiles_wide = hp.wide_diag ? std::max(1, tune.k_flush / (2 * kt_of(engine, true))) : hp.k_flush_tiles;
     hp.slots = ms_max == 1 ? 2 : (ms_max == 2 ? 3 : 4);     // operand blocks per stage for the widest strip
     hp.n_acc = ms_max <= 2 ? 2 : 1;                        // TMEM accumulators (each <= 256 columns)
@@ -1922,7 +1961,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     hp.limit_ns = wait_limit_ns();
     const int bar_bytes = 1024;
     const int avail = kSmemMax - 1024 - bar_bytes;
-    const int op_slot = kBlk * kt_of(engine, pk != nullptr), pk_slot = 64 * kt_of(engine);
+    const int op_slot = kBlk * kt_of(engine, rows128), pk_slot = 64 * kt_of(engine);
     int staging = 0;
     bool all_fold = nj > 0;
     for (int j = 0; j < nj; ++j) {
@@ -1953,10 +1992,10 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     if (engine == kFusedPair)
     {
         // the Gram layout's doubles and singles alternate best on an odd pair count; fold items are alike
-        bool odd = pk && !all_fold;
+        bool odd = rows128 && !all_fold;
         if (has_launch_ent && launch_ent.odd_pairs >= 0) odd = launch_ent.odd_pairs == 1;
-        return pk ? launch_pair<true>(hp, items, tune.n_ctas, smem, odd, st)
-                  : launch_pair<false>(hp, items, tune.n_ctas, smem, odd, st);
+        return rows128 ? launch_pair<true>(hp, items, tune.n_ctas, smem, odd, st)
+                       : launch_pair<false>(hp, items, tune.n_ctas, smem, odd, st);
     }
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     switch (engine) {
@@ -2004,7 +2043,8 @@ int xe_tune_table_set(const xe_tune_entry *entries, int32_t n) {
         const bool pow2 = e.t_bucket >= 128 && (e.t_bucket & (e.t_bucket - 1)) == 0;
         if (e.n_inputs < 16 || e.n_inputs > 4096 || e.n_inputs % 16 || !pow2 || e.mode < XE_TUNE_PACKETS ||
             e.mode > XE_TUNE_FRAMES || e.layout < XE_LAYOUT_AUTO ||
-            e.layout > XE_LAYOUT_FOLD || e.pairs < 0 || e.pairs > 4096 || e.odd_pairs < -1 || e.odd_pairs > 1 ||
+            e.layout > XE_LAYOUT_FRAME_BLOCKS || (e.layout == XE_LAYOUT_FRAME_BLOCKS && e.mode != XE_TUNE_FRAMES) ||
+            e.pairs < 0 || e.pairs > 4096 || e.odd_pairs < -1 || e.odd_pairs > 1 ||
             e.k_flush < 0 || e.k_flush > corr::kMaxKFlush || e.k_flush % corr::kKtMax)
             return XE_EINVAL;
         for (int k2 = 0; k2 < k; ++k2)

@@ -176,6 +176,12 @@ __device__ __forceinline__ uint4 ld_stream_16(const uint8_t *ptr) {
     return v;
 }
 
+// Adds v to *ptr in L2 (relaxed, device scope) without returning the old value: the thread does not
+// wait for the line, so an epilogue that adds into existing visibilities keeps no loads in flight.
+__device__ __forceinline__ void red_add(int32_t *ptr, int32_t v) {
+    asm volatile("red.global.add.s32 [%0], %1;" ::"l"(ptr), "r"(v));
+}
+
 // Hint: bring the 128-byte line holding ptr into L2 (no register result, no fault on the address).
 __device__ __forceinline__ void prefetch_l2(const void *ptr) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));

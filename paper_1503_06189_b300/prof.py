@@ -5,6 +5,7 @@
     python -m paper_1503_06189_b300.prof normalize --n 256 --f 128 --iters 3
     python -m paper_1503_06189_b300.prof packets   --n 256 --f 128 --t 4096 --iters 3
     python -m paper_1503_06189_b300.prof flags     --n 256 --f 256 --t 4096 --iters 3
+    python -m paper_1503_06189_b300.prof shift     --n 256 --f 128 --t 4096 --iters 3 [--spread 64] [--uniform]
 
 Inputs are uniform random bytes generated on the device; sizes default to a frame larger than L2
 (128 MiB) so that DRAM counters are meaningful, while the device footprint stays at a few GB.
@@ -22,7 +23,8 @@ import paper_1503_06189_b300 as xe
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("op", choices=["correlate", "assemble", "normalize", "packets", "flags", "mma_legacy"])
+    ap.add_argument("op", choices=["correlate", "assemble", "normalize", "packets", "flags", "mma_legacy",
+                                       "shift"])
     ap.add_argument("--n", type=int, default=256)
     ap.add_argument("--f", type=int, default=128)
     ap.add_argument("--t", type=int, default=4096)
@@ -34,6 +36,8 @@ def main(argv=None):
                     help="packets: keep arrival (sequence-major) order or sort them group-major")
     ap.add_argument("--align", action="store_true",
                     help="packets: re-lay the packets at a 128-byte multiple stride with 128-byte aligned payloads")
+    ap.add_argument("--spread", type=int, default=64, help="shift: delays drawn from 0 .. spread samples")
+    ap.add_argument("--uniform", action="store_true", help="shift: one delay per block of 16 inputs")
     a = ap.parse_args(argv)
     dev = torch.device("cuda", 0)
     g = torch.Generator(device=dev)
@@ -153,6 +157,23 @@ def main(argv=None):
             total = blocks * 8 * iters * 8 * ops
             print(f"{name}: {total / ms / 1e9:.1f} T int-op/s ({blocks} CTAs x 8 warps x {iters} x 8 "
                   f"instructions in {ms:.3f} ms)", flush=True)
+    elif a.op == "shift":
+        # per-input sample delays (each input its own, or one per block of 16 inputs); 2 bytes per sample
+        import numpy as np
+        rng = np.random.default_rng(3)
+        d = rng.integers(0, a.spread + 1, N // 16 if a.uniform else N)
+        d = np.repeat(d, 16) if a.uniform else d
+        out = torch.empty_like(frame)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.iters)]
+        for e0, e1 in evs:
+            e0.record()
+            xe.xe_time_shift(frame, s, d, out)
+            e1.record()
+        torch.cuda.synchronize()
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        best = min(ms[1:] if len(ms) > 1 else ms)
+        print(f"shift N={N} F={F} T={T} spread={a.spread} uniform={a.uniform}: best {best:.4f} ms, "
+              f"{2 * frame.numel() / best / 1e6:.1f} GB/s", flush=True)
     else:
         lost = torch.zeros(F, dtype=torch.int32, device=dev)
         out = torch.empty((F, P, 2), dtype=torch.float32, device=dev)

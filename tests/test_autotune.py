@@ -50,7 +50,7 @@ def test_items_per_channel_of_the_gram_layouts():
     assert autotune.items_per_channel(256, xe.XE_LAYOUT_GRAM, 32768) == 1.5    # twins from T >= 16384
     assert autotune.items_per_channel(256, xe.XE_LAYOUT_AUTO, 4096) == 1       # fold at N > 128
     assert autotune.items_per_channel(64, xe.XE_LAYOUT_AUTO, 4096) == 1        # one block: wide single
-    assert autotune.items_per_channel(2048, xe.XE_LAYOUT_AUTO, 0, packets=False) == 136
+    assert autotune.items_per_channel(2048, xe.XE_LAYOUT_FRAME_BLOCKS, 0) == 136   # 256-sample kernel
 
 
 def test_candidate_sets():
@@ -59,8 +59,12 @@ def test_candidate_sets():
     assert {c["odd_pairs"] for c in p256} == {0, 1}
     p64 = autotune.packet_candidates(64)
     assert {c["layout"] for c in p64} == {xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE}
-    f = autotune.frame_candidates(256, 100)           # 300 blocks: 5 rounds on 74 pairs, 60 pairs suffice
-    assert {c["pairs"] for c in f} == {0, 60}
+    f = autotune.frame_candidates(256, 100)
+    assert {c["layout"] for c in f} == {xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM, xe.XE_LAYOUT_FRAME_BLOCKS}
+    blk = [c for c in f if c["layout"] == xe.XE_LAYOUT_FRAME_BLOCKS]
+    assert {c["pairs"] for c in blk} == {0, 60}       # 300 blocks: 5 rounds on 74 pairs, 60 pairs suffice
+    # T % 4 != 0: only the 256-sample kernel reads such a frame
+    assert {c["layout"] for c in autotune.frame_candidates(256, 100, 1030)} == {xe.XE_LAYOUT_FRAME_BLOCKS}
 
 
 def test_probe_channels_aim_for_rounds_within_bytes():
@@ -108,13 +112,14 @@ def test_table_picks_fastest_candidate_caches_and_installs(tmp_path, monkeypatch
 def test_tune_table_rejects_bad_entries():
     good = dict(n_inputs=256, t_bucket=4096, mode=0, layout=4, pairs=0, odd_pairs=-1, k_flush=0)
     for bad in (dict(good, t_bucket=4000), dict(good, n_inputs=250), dict(good, layout=9), dict(good, mode=2),
-                dict(good, k_flush=100), dict(good, odd_pairs=2)):
+                dict(good, k_flush=100), dict(good, odd_pairs=2),
+                dict(good, layout=xe.XE_LAYOUT_FRAME_BLOCKS)):           # the 256-sample kernel: frames only
         with pytest.raises(xe.XeError) as e:
             xe.xe_tune_table_set([bad])
         assert e.value.status == xe.XE_EINVAL
     with pytest.raises(xe.XeError):
         xe.xe_tune_table_set([good, dict(good)])                  # two entries for one (N, bucket, mode)
-    xe.xe_tune_table_set([good, dict(good, mode=1)])
+    xe.xe_tune_table_set([good, dict(good, mode=1, layout=xe.XE_LAYOUT_FRAME_BLOCKS)])
     assert len(xe.xe_tune_table_get()) == 2
     xe.xe_tune_table_set([])
     assert xe.xe_tune_table_get() == []

@@ -1,5 +1,7 @@
 """The time-shift stage (xe_time_shift, xe_time_shift_counts) through the C ABI against the oracle
-(GPU). The shifted frame and the counters are integer work: bit-exact. End to end, packets are
+(GPU). The shifted frame and the counters are integer work: bit-exact. Delay spreads up to 256
+samples per 128 inputs run the shared-memory window kernel (TMA boxes, zero fill before the frame's
+start), larger ones the gather kernel; both are covered. End to end, packets are
 assembled, shifted, correlated and normalised on the device and compared with the same chain on the
 oracle (correlation bit-exact, normalisation within 1e-6 relative)."""
 import numpy as np
@@ -16,11 +18,19 @@ pytestmark = pytest.mark.gpu
 REL_TOL = 1e-6
 
 
-def _delays(rng, N, T, uniform_blocks=0):
-    d = rng.integers(0, T + 1, N)
-    d[0], d[-1] = 0, T                                      # no shift, and nothing left
+def _delays(rng, N, T, uniform_blocks=0, spread=None):
+    """Delays in [0, T] (gather kernel), or within `spread` of a random offset per 128 inputs
+    (window kernel when spread <= 256)."""
+    if spread is None:
+        d = rng.integers(0, T + 1, N)
+        d[0], d[-1] = 0, T                                  # no shift, and nothing left
+    else:
+        off = rng.integers(0, max(1, T - spread) + 1, (N + 127) // 128)
+        off[0] = 0                                          # the first block starts unshifted
+        d = np.minimum(np.repeat(off, 128)[:N] + rng.integers(0, spread + 1, N), T)
+        d[0] = 0
     for b in range(uniform_blocks):                         # some blocks of 16 inputs share one delay
-        d[16 * b:16 * b + 16] = rng.integers(0, T + 1)
+        d[16 * b:16 * b + 16] = d[16 * b]
     return d
 
 
@@ -38,6 +48,19 @@ def test_time_shift_matches_oracle(N, F, T, ub):
     rng = np.random.default_rng(N + T)
     fr = synth.uniform_frame(N, F, T, 3 * N + T)
     d = _delays(rng, N, T, ub)
+    got = _shift_gpu(fr, d).cpu().numpy()
+    np.testing.assert_array_equal(got, oracle.time_shift(fr, d))
+
+
+@pytest.mark.parametrize("N,F,T,ub,spread", [(16, 3, 37, 0, 5), (48, 2, 300, 1, 40), (64, 5, 129, 2, 0),
+                                             (256, 8, 4100, 8, 256), (272, 3, 513, 3, 17), (1024, 2, 1000, 20, 200),
+                                             (128, 4, 700, 4, 256)])
+def test_time_shift_window_kernel_matches_oracle(N, F, T, ub, spread):
+    """Spreads of at most 256 samples per 128 inputs: the window kernel, with tiles cut by T and N,
+    boxes narrower than 128 inputs (N < 128), and delays larger than the tile's first row."""
+    rng = np.random.default_rng(N + T + spread)
+    fr = synth.uniform_frame(N, F, T, 5 * N + T)
+    d = _delays(rng, N, T, ub, spread)
     got = _shift_gpu(fr, d).cpu().numpy()
     np.testing.assert_array_equal(got, oracle.time_shift(fr, d))
 
