@@ -520,6 +520,7 @@ def run_xe(args):
         "realtime_factor": FR * T / SAMPLE_RATE / (ms / 1e3),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": traffic,
+                     "peak_burst": 2.0 * pk["bf16_tflops"], "frac_burst": achieved / (2.0 * pk["bf16_tflops"]),
                      "kernel": f"xe_correlate_packets over {G} frame(s) per call (index kernels + packet-mode "
                                "CTA-pair tcgen05 correlation), 8 int ops per CMAC, timed by CUDA events around each call",
                      "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},
@@ -915,6 +916,7 @@ def run_config(args):
                    "l2": "256 MiB written between steps" + ("; the tiny frame itself fits in L2" if cfg == 1 else "")},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops, "traffic": None,
+                     "peak_burst": 2.0 * pk["bf16_tflops"], "frac_burst": achieved / (2.0 * pk["bf16_tflops"]),
                      "useful_mma_fraction": useful_mma_fraction(shapes, layouts),
                      "kernel": "xe_correlate_batched (CTA-pair tcgen05 correlation), 8 int ops per CMAC",
                      "peak_source": f"{how}: 2 x bf16_tflops_sustained (FP8 kind::f8f6f4 dense)"},

@@ -228,8 +228,12 @@ int xe_probe_mma_legacy(int32_t kind, int32_t blocks, int32_t iters, int32_t *si
 #define XE_LAYOUT_GRAM 1       /* Gram blocks: doubles and singles, twins from T >= 16384, wide singles below */
 #define XE_LAYOUT_GRAM_TWIN 2  /* Gram blocks, twins at any T */
 #define XE_LAYOUT_GRAM_WIDE 3  /* Gram blocks, wide singles at any T */
-#define XE_LAYOUT_FOLD 4       /* one fold item per whole 256-input super-block (N > 128; else GRAM) */
+#define XE_LAYOUT_FOLD 4       /* one fold item per whole 256-input super-block (N > 128; else GRAM); see
+                                  XE_LAYOUT_FOLD_SPLIT for launches whose last round would be ragged */
 #define XE_LAYOUT_FRAME_BLOCKS 5   /* frame mode: every Gram block its own item, 256-sample stages */
+#define XE_LAYOUT_FOLD_SPLIT 6     /* fold, and a one-job launch of 129-256 inputs splits its channels' samples
+                                      evenly over the CTA pairs (pieces add through L2); AUTO and FOLD do so
+                                      when whole channels would leave over a tenth of the last round idle */
 
 /*
  * One entry of the library's tuning table: the choices of the CTA-pair engine for jobs with N inputs

@@ -23,6 +23,7 @@ XE_ENGINE_AUTO, XE_ENGINE_UNPACKED, XE_ENGINE_FUSED, XE_ENGINE_UNPACKED_K, XE_EN
 XE_ENGINE_LEGACY_S4, XE_ENGINE_LEGACY_S8 = 5, 6
 XE_LAYOUT_AUTO, XE_LAYOUT_GRAM, XE_LAYOUT_GRAM_TWIN, XE_LAYOUT_GRAM_WIDE, XE_LAYOUT_FOLD = 0, 1, 2, 3, 4
 XE_LAYOUT_FRAME_BLOCKS = 5
+XE_LAYOUT_FOLD_SPLIT = 6
 XE_TUNE_MAX_ENTRIES = 256
 XE_TUNE_PACKETS, XE_TUNE_FRAMES = 0, 1
 

@@ -2,8 +2,9 @@
 (N, T-bucket) and mode. It fills libxe's tuning table (xe_tune_entry in include/xe.h):
 
 - packet mode (xe_correlate_packets and the serving loop): the work-item layout -- fold items over
-  whole 256-input super-blocks, Gram blocks with twins, or Gram blocks with wide singles -- and
-  whether the launch takes an odd number of CTA pairs;
+  whole 256-input super-blocks (whole, or with a channel's samples split evenly over the CTA pairs),
+  Gram blocks with twins, or Gram blocks with wide singles -- and whether the launch takes an odd
+  number of CTA pairs;
 - frame mode (xe_correlate, xe_correlate_batched): the kernel and layout -- the 128-sample kernel
   (the packet-mode kernel reading the frame in 4-sample slots) with any of those layouts, or the
   256-sample frame kernel with every Gram block its own item -- the number of CTA pairs (fewer
@@ -52,7 +53,7 @@ def items_per_channel(n_inputs: int, layout: int, n_time: int) -> float:
     nb = blocks(n_inputs)
     if layout == xe.XE_LAYOUT_FRAME_BLOCKS:
         return nb * (nb + 1) / 2
-    fold = nb >= 2 and layout in (xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_FOLD)
+    fold = nb >= 2 and layout in (xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_FOLD_SPLIT)
     if fold:
         return nb // 2 + (nb & 1) + sum(max(0, nb - 2 * (r // 2 + 1)) for r in range(nb))
     twin = layout == xe.XE_LAYOUT_GRAM_TWIN or (layout in (xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_GRAM)
@@ -62,10 +63,12 @@ def items_per_channel(n_inputs: int, layout: int, n_time: int) -> float:
 
 
 def row_layouts(n_inputs: int) -> list[int]:
-    """Layouts of the 128-sample kernel worth measuring: fold or Gram blocks above 128 inputs, twins
-    or wide singles for a single block."""
-    return [xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM] if blocks(n_inputs) >= 2 else \
-        [xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE]
+    """Layouts of the 128-sample kernel worth measuring: fold or Gram blocks above 128 inputs (and
+    the balanced split where a channel is one fold item), twins or wide singles for a single block."""
+    nb = blocks(n_inputs)
+    if nb == 1:
+        return [xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE]
+    return [xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM] + ([xe.XE_LAYOUT_FOLD_SPLIT] if nb == 2 else [])
 
 
 def packet_candidates(n_inputs: int) -> list[dict]:

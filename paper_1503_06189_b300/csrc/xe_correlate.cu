@@ -86,6 +86,10 @@ struct Params {
     int32_t op_stages, pk_stages, slots, n_acc;
     int32_t fold;                 // some job has the fold layout: three operand slots, transpose staging
     int32_t frame_rows;           // 128-sample kernel reading assembled frames (no owner tables)
+    // balanced split (one job of fold items, one per channel): pair q takes stages
+    // [q split_u, (q + 1) split_u) of the job's channel-major F x k_tiles stages, as up to
+    // split_items items (pieces of consecutive channels); 0 = off
+    int32_t split_u, split_pairs, split_items;
     int *status;
     int *counter;            // work-item counter, zero at launch
     uint64_t limit_ns;
@@ -686,6 +690,9 @@ struct PairItem {
     bool twin;   // the last diagonal blocks of channels f and f + 1
     bool wide;   // a single diagonal block in stages of 2 kKt samples
     bool fold;   // a fold item (fold layout only)
+    bool empty;  // balanced split: no further item of this pair
+    int kt0;     // balanced split: first stage of the piece (else 0)
+    int kt_n;    // balanced split: stages of the piece (else -1: the job's whole integration)
 };
 
 // Work items of a frame-mode job: every 256x256 block (R, C >= R) of every channel its own item.
@@ -708,8 +715,30 @@ struct PairItem {
 // - a half super-block at the end (N mod 256 in (0, 128]) as a Gram diagonal single;
 // - the Gram blocks between different super-blocks as singles (R, C) with R / 2 < C / 2.
 // Each fold item and single fills one TMEM half, so consecutive items alternate halves.
+// (kSplit: the 128-sample kernel, the only one that runs balanced splits)
+template <bool kSplit>
 __device__ __forceinline__ PairItem decode_pair_item(const Params &p, int g) {
     PairItem it;
+    it.empty = false;
+    it.kt0 = 0;
+    it.kt_n = -1;
+    if (kSplit && p.split_u > 0) {            // balanced split: piece k of pair q's stage range
+        const Job &jb = p.jobs[0];
+        const int q = g % p.split_pairs, k = g / p.split_pairs, K = jb.k_tiles;
+        const int64_t total = (int64_t)jb.n_chan * K;
+        const int64_t start = (int64_t)q * p.split_u, end = min(start + p.split_u, total);
+        const int c = (int)(start / K) + k;
+        const int64_t s0 = max(start, (int64_t)c * K), s1 = min(end, (int64_t)(c + 1) * K);
+        it.job = 0;
+        it.f = c;
+        it.R = it.C = 0;
+        it.dbl = it.twin = it.wide = false;
+        it.fold = true;
+        it.empty = c >= jb.n_chan || s0 >= s1;
+        it.kt0 = (int)(s0 - (int64_t)c * K);
+        it.kt_n = (int)(s1 - s0);
+        return it;
+    }
     int j = 0;
     while (j + 1 < p.n_jobs && g >= p.jobs[j + 1].item_begin) ++j;
     const Job &jb = p.jobs[j];
@@ -808,9 +837,10 @@ __device__ __forceinline__ PairItem decode_pair_item(const Params &p, int g) {
 }
 
 // stages of an item and its drain interval in stages
-__device__ __forceinline__ void item_stages(const Params &p, const Job &jb, bool wide, int &k_tiles, int &flush) {
-    k_tiles = wide ? jb.k_tiles_wide : jb.k_tiles;
-    flush = wide ? p.k_flush_tiles_wide : p.k_flush_tiles;
+__device__ __forceinline__ void item_stages(const Params &p, const Job &jb, const PairItem &it, int &k_tiles,
+                                            int &flush) {
+    k_tiles = it.kt_n >= 0 ? it.kt_n : (it.wide ? jb.k_tiles_wide : jb.k_tiles);
+    flush = it.wide ? p.k_flush_tiles_wide : p.k_flush_tiles;
 }
 
 // Walks the (item, k-tile) stages of one pair in order (frame mode: forwarder and L2 prefetch).
@@ -822,7 +852,7 @@ struct PairCursor {
         if (g < p.n_items) load(p);
     }
     __device__ __forceinline__ void load(const Params &p) {
-        const PairItem it = decode_pair_item(p, g);
+        const PairItem it = decode_pair_item<false>(p, g);
         job = it.job;
         f = it.f;
         R = it.R;
@@ -868,13 +898,17 @@ struct PairLoader {
     int64_t pstride;
 
     __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
-        const PairItem it = decode_pair_item(p, g);
+        const PairItem it = decode_pair_item<kPackets>(p, g);
+        if (it.empty) {                       // balanced split: this pair's pieces are done
+            g = p.n_items;
+            return;
+        }
         const Job &jb = p.jobs[it.job];
         const int N = jb.n_inputs, F = jb.n_chan;
         kt = 0;
         wide = kPackets && it.wide;
         const bool twin = kPackets && it.twin;
-        k_tiles = wide ? jb.k_tiles_wide : jb.k_tiles;
+        k_tiles = it.kt_n >= 0 ? it.kt_n : (wide ? jb.k_tiles_wide : jb.k_tiles);
         int ca, cb;
         if (kPackets && it.fold) {
             // odd rows take the CTA's second 64 inputs first: their first stores then go to chunks
@@ -913,6 +947,12 @@ struct PairLoader {
         }
         pa = base + ca;
         pb = base + cb + (twin ? N : 0);      // a twin's B block: channel f + 1, N bytes on
+        if constexpr (kPackets) {             // (the balanced split runs in this kernel only)
+            if (it.kt0) {                     // a piece of a split integration starts kt0 stages in
+                own += (uintptr_t)it.kt0 * S::kKt;
+                s_left -= it.kt0 * (S::kKt / 4);
+            }
+        }
     }
     __device__ __forceinline__ void start(const Params &p, int pair, uint32_t rank, int t_row, int c) {
         g = pair;
@@ -1103,10 +1143,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             uint32_t acc = 0, acc_ph = 0;
             bool ok = true;
             for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-                const PairItem it = decode_pair_item(p, g);
+                const PairItem it = decode_pair_item<kPackets>(p, g);
+                if (it.empty) break;
                 const bool dbl = kPackets && it.dbl;   // frame mode never runs doubles or twins
                 int kt_n, fl;
-                item_stages(p, p.jobs[it.job], kPackets && it.wide, kt_n, fl);
+                item_stages(p, p.jobs[it.job], it, kt_n, fl);
                 for (int k0 = 0; k0 < kt_n && ok; k0 += fl) {
                     for (int sub = 0; sub < (dbl ? 2 : 1); ++sub) {   // a double fills both halves
                         if (*abort_flag || !wait(&epi_done[acc], (acc_ph >> acc) & 1u)) { ok = false; break; }
@@ -1125,7 +1166,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             uint32_t s = 0, ph = 0, acc = 0, acc_ph = 0;
             bool ok = true;
             for (int g = pair; g < p.n_items && ok; g += n_pairs) {
-                const PairItem it = decode_pair_item(p, g);
+                const PairItem it = decode_pair_item<kPackets>(p, g);
+                if (it.empty) break;
                 const bool dbl = kPackets && it.dbl;   // frame mode never runs doubles, twins or folds
                 const bool twin = kPackets && it.twin;
                 const bool fold = kPackets && it.fold;
@@ -1138,7 +1180,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 const uint32_t b_slot = it.R == it.C && !twin ? 0u : 1u;
                 const uint32_t acc2 = acc ^ 1u;
                 int kt_n, fl;
-                item_stages(p, jb, wide, kt_n, fl);
+                item_stages(p, jb, it, kt_n, fl);
                 for (int k0 = 0; k0 < kt_n && ok; k0 += fl) {
                     const int k1 = min(kt_n, k0 + fl);
                     if (*abort_flag || !wait(&acc_empty[acc], ((acc_ph >> acc) & 1u) ^ 1u)) { ok = false; break; }
@@ -1203,7 +1245,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         // every item and leaves only together with the others: a warp that failed a wait skips the
         // work of Gram items and says so at the next fold item's first barrier, where all decide.
         for (int g = pair; g < p.n_items; g += n_pairs) {
-            const PairItem it = decode_pair_item(p, g);
+            const PairItem it = decode_pair_item<kPackets>(p, g);
+            if (it.empty) break;
             if (!ok && !(kPackets && it.fold)) continue;
             const bool dbl = kPackets && it.dbl;     // frame mode never runs doubles, twins or folds
             const bool twin = kPackets && it.twin;
@@ -1211,7 +1254,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             const int N = jb.n_inputs;
             int32_t *vis_f = jb.vis + (size_t)it.f * (size_t)npairs(N) * 2;
             int kt_n, fl;
-            item_stages(p, jb, kPackets && it.wide, kt_n, fl);
+            item_stages(p, jb, it, kt_n, fl);
             if (kPackets && it.fold) {
                 // ------------------------------------------------------------ fold item
                 // This CTA holds rows 128 rank + m of D (scaled by 16) over the super-block's 256
@@ -1720,13 +1763,13 @@ static int launch_gemm(const Params &hp, int ctas, int smem, cudaStream_t st) {
 }
 
 // Pair engine: as many 2-CTA clusters as can be resident at once (each CTA fills an SM), one per
-// work item at most.
+// work item at most, at most n_ctas / 2 if n_ctas > 0.
 template <bool kPackets>
-static int launch_pair(const Params &hp, int items, int n_ctas, int smem, bool odd_pairs, cudaStream_t st) {
+static int pair_count(int items, int n_ctas, bool odd_pairs, int *out) {
     static int max_pairs[64] = {};
     int dev = 0;
     XE_TRY_CUDA(cudaGetDevice(&dev));
-    if (dev >= 64) return XE_EINVAL;
+    if (dev < 0 || dev >= 64) return XE_EINVAL;
     if (!max_pairs[dev]) {
         XE_TRY_CUDA(cudaFuncSetAttribute(correlate_pair_kernel<kPackets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemMax));
@@ -1750,6 +1793,14 @@ static int launch_pair(const Params &hp, int items, int n_ctas, int smem, bool o
     // the packet-mode Gram layout interleaves doubles and singles channel by channel: an odd pair
     // count makes every pair alternate between the two kinds (fold items are all alike)
     if (odd_pairs && pairs > 1 && pairs % 2 == 0) --pairs;
+    *out = pairs;
+    return XE_OK;
+}
+
+template <bool kPackets>
+static int launch_pair(const Params &hp, int items, int n_ctas, int smem, bool odd_pairs, cudaStream_t st) {
+    int pairs = 0;
+    if (int e = pair_count<kPackets>(items, n_ctas, odd_pairs, &pairs)) return e;
     correlate_pair_kernel<kPackets><<<2 * pairs, PairShape<kPackets>::kThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
@@ -1832,6 +1883,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     int *counter = reinterpret_cast<int *>(base);
     uint8_t *ybase = base + kWsHeader;
     int items = 0, nj = 0, ms_max = 1;
+    int job_layout[XE_MAX_JOBS] = {};
     for (int j = 0; j < n_jobs; ++j) {
         const xe_shape &s = jobs[j].s;
         const JobGeom g = geom(s, engine);
@@ -1895,7 +1947,9 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
             d.fold = 0;
             int layout = has_ent[j] ? ent[j].layout : XE_LAYOUT_AUTO;
             if (layout == XE_LAYOUT_FRAME_BLOCKS) layout = XE_LAYOUT_AUTO;   // a job in a 128-sample launch
-            if (rows128 && d.nb >= 2 && (layout == XE_LAYOUT_AUTO || layout == XE_LAYOUT_FOLD)) {
+            job_layout[nj - 1] = layout;
+            if (rows128 && d.nb >= 2 &&
+                (layout == XE_LAYOUT_AUTO || layout == XE_LAYOUT_FOLD || layout == XE_LAYOUT_FOLD_SPLIT)) {
                 // fold layout: per channel S2 / 2 fold items, a Gram diagonal single for an odd last
                 // block, and the Gram blocks (R, C) between different super-blocks (R / 2 < C / 2)
                 d.fold = 1;
@@ -1994,8 +2048,34 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         // the Gram layout's doubles and singles alternate best on an odd pair count; fold items are alike
         bool odd = rows128 && !all_fold;
         if (has_launch_ent && launch_ent.odd_pairs >= 0) odd = launch_ent.odd_pairs == 1;
-        return rows128 ? launch_pair<true>(hp, items, tune.n_ctas, smem, odd, st)
-                       : launch_pair<false>(hp, items, tune.n_ctas, smem, odd, st);
+        if (!rows128) return launch_pair<false>(hp, items, tune.n_ctas, smem, odd, st);
+        // Balanced split: a launch of one job whose channels are one fold item each (129-256
+        // inputs) hands every pair an equal share of the job's channel x stage range, as pieces of
+        // consecutive channels, when whole items would leave more than a tenth of the last round's
+        // pairs idle (configuration 2: 64 channels on 74 pairs), or always with XE_LAYOUT_FOLD_SPLIT.
+        // Pieces add their sums with L2 reductions, so a call that does not accumulate first
+        // clears its visibilities.
+        Job &d0 = hp.jobs[0];
+        if (nj == 1 && d0.fold && d0.nb == 2) {
+            int pairs = 0;
+            if (int e = pair_count<true>(items, tune.n_ctas, false, &pairs)) return e;
+            const int rounds = (items + pairs - 1) / pairs;
+            const bool ragged = (double)items < 0.9 * (double)rounds * (double)pairs;
+            if (job_layout[0] == XE_LAYOUT_FOLD_SPLIT || ragged) {
+                const int64_t total = (int64_t)d0.n_chan * d0.k_tiles;
+                hp.split_pairs = pairs;
+                hp.split_u = (int)((total + pairs - 1) / pairs);
+                hp.split_items = (hp.split_u + d0.k_tiles - 1) / d0.k_tiles + 1;
+                if ((int64_t)pairs * hp.split_items > INT32_MAX / 2) return XE_EINVAL;
+                hp.n_items = items = pairs * hp.split_items;
+                if (!d0.accumulate) {
+                    XE_TRY_CUDA(cudaMemsetAsync(d0.vis, 0, (size_t)d0.n_chan * npairs(d0.n_inputs) * 8, st));
+                    d0.accumulate = 1;
+                }
+                return launch_pair<true>(hp, items, 2 * pairs, smem, false, st);
+            }
+        }
+        return launch_pair<true>(hp, items, tune.n_ctas, smem, odd, st);
     }
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     switch (engine) {
@@ -2043,7 +2123,7 @@ int xe_tune_table_set(const xe_tune_entry *entries, int32_t n) {
         const bool pow2 = e.t_bucket >= 128 && (e.t_bucket & (e.t_bucket - 1)) == 0;
         if (e.n_inputs < 16 || e.n_inputs > 4096 || e.n_inputs % 16 || !pow2 || e.mode < XE_TUNE_PACKETS ||
             e.mode > XE_TUNE_FRAMES || e.layout < XE_LAYOUT_AUTO ||
-            e.layout > XE_LAYOUT_FRAME_BLOCKS || (e.layout == XE_LAYOUT_FRAME_BLOCKS && e.mode != XE_TUNE_FRAMES) ||
+            e.layout > XE_LAYOUT_FOLD_SPLIT || (e.layout == XE_LAYOUT_FRAME_BLOCKS && e.mode != XE_TUNE_FRAMES) ||
             e.pairs < 0 || e.pairs > 4096 || e.odd_pairs < -1 || e.odd_pairs > 1 ||
             e.k_flush < 0 || e.k_flush > corr::kMaxKFlush || e.k_flush % corr::kKtMax)
             return XE_EINVAL;

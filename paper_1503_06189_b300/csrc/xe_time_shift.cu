@@ -53,9 +53,16 @@ __global__ void __launch_bounds__(kThreads) shift_window_kernel(const __grid_con
                                                                  uint64_t limit_ns, int *status) {
     extern __shared__ __align__(1024) uint8_t win[];
     __shared__ __align__(8) uint64_t bar;
+    // per input: its window row offset e[n] = dmax of its block - d[n] (0 .. kMaxSpread), and per 16
+    // inputs the one-delay flag, copied once per CTA: the parameter block is read through the constant
+    // cache, which serialises lanes that read different addresses
+    uint16_t *se = reinterpret_cast<uint16_t *>(win + kWinBytes);
+    uint8_t *su = win + kWinBytes + 2 * N;
     const int nb = (N + 127) / 128, n_tt = (T + kTileRows - 1) / kTileRows;
     const int64_t tiles = (int64_t)F * nb * n_tt;
     const int v = threadIdx.x & 7, r0 = threadIdx.x >> 3;
+    for (int n = threadIdx.x; n < N; n += kThreads) se[n] = (uint16_t)(dl.dmax[n / 128] - dl.d[n]);
+    for (int g = threadIdx.x; g < N / 16; g += kThreads) su[g] = dl.uniform[g];
     if (threadIdx.x == 0) {
         dev::mbar_init(&bar, 1);
         dev::fence_mbar_init();
@@ -85,21 +92,36 @@ __global__ void __launch_bounds__(kThreads) shift_window_kernel(const __grid_con
         if (16 * v < box_x && n0 < N) {
             uint8_t *dst = out + ((size_t)t0 * F + f) * N + n0;
             const size_t rstride = (size_t)F * N;
-            if (dl.uniform[n0 / 16]) {
-                const int e = dmax - dl.d[n0];
+            if (su[n0 / 16]) {
+                const int e = se[n0];
                 for (int r = r0; r < rows; r += kThreads / 8) {
                     const uint4 x = *reinterpret_cast<const uint4 *>(win + (r + e) * box_x + 16 * v);
                     __stcs(reinterpret_cast<uint4 *>(dst + r * rstride), x);
                 }
             } else {
-                int base[16];                       // window offset of byte k at tile row 0
+                // Byte j of the loop reads input 16 v + k with k = (j + 4 rl) mod 16, rl = this lane's
+                // row within its warp: the 32 lanes of a warp then read 32 different banks (with
+                // k = j for all lanes they shared 8 banks, four rows apart). The words are assembled
+                // in that rotated order and rotated back by rl words before the store.
+                const int rl = r0 & 3;
+                int base[16];                       // window offset of loop byte j at tile row 0
 #pragma unroll
-                for (int k = 0; k < 16; ++k) base[k] = (dmax - dl.d[n0 + k]) * box_x + 16 * v + k;
+                for (int j = 0; j < 16; ++j) {
+                    const int k = (j + 4 * rl) & 15;
+                    base[j] = se[n0 + k] * box_x + 16 * v + k;
+                }
                 for (int r = r0; r < rows; r += kThreads / 8) {
                     uint32_t w[4] = {0, 0, 0, 0};
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) w[k >> 2] |= (uint32_t)win[base[k] + r * box_x] << (8 * (k & 3));
-                    __stcs(reinterpret_cast<uint4 *>(dst + r * rstride), make_uint4(w[0], w[1], w[2], w[3]));
+                    for (int j = 0; j < 16; ++j) w[j >> 2] |= (uint32_t)win[base[j] + r * box_x] << (8 * (j & 3));
+                    // rotated word i holds inputs 4 ((i + rl) mod 4) ..: output word o = w[(o - rl) mod 4]
+                    uint32_t o[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int s0 = (i - rl) & 3;
+                        o[i] = s0 == 0 ? w[0] : s0 == 1 ? w[1] : s0 == 2 ? w[2] : w[3];
+                    }
+                    __stcs(reinterpret_cast<uint4 *>(dst + r * rstride), make_uint4(o[0], o[1], o[2], o[3]));
                 }
             }
         }
@@ -208,19 +230,24 @@ int xe_time_shift(const uint8_t *in, xe_shape s, const int32_t *delays, uint8_t 
         if (encode_tiled(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(in), dims, strides, box,
                          CU_TENSOR_MAP_SWIZZLE_NONE) != XE_OK)
             return XE_EINVAL;
+        // dynamic shared memory: the window, then the per-input offsets and the one-delay flags
+        const int smem = shift::kWinBytes + 2 * s.n_inputs + s.n_inputs / 16;
         static bool attr_set[64] = {};
         int dev = 0;
         XE_TRY_CUDA(cudaGetDevice(&dev));
         if (dev < 0 || dev >= 64) return XE_EINVAL;
         if (!attr_set[dev]) {
             XE_TRY_CUDA(cudaFuncSetAttribute(shift::shift_window_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             shift::kWinBytes));
+                                             shift::kWinBytes + 2 * 4096 + 4096 / 16));
             attr_set[dev] = true;
         }
+        int per_sm = 0;
+        XE_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, shift::shift_window_kernel, shift::kThreads,
+                                                                  smem));
         const int64_t tiles = (int64_t)s.n_chan * ((s.n_inputs + 127) / 128) *
                               ((s.n_time + shift::kTileRows - 1) / shift::kTileRows);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * 4));
-        shift::shift_window_kernel<<<grid, shift::kThreads, shift::kWinBytes, st>>>(
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)sm_count() * std::max(1, per_sm)));
+        shift::shift_window_kernel<<<grid, shift::kThreads, smem, st>>>(
             map, out, s.n_inputs, s.n_chan, s.n_time, box_x, dl, wait_limit_ns(), status);
     } else {
         const int64_t work = (int64_t)s.n_time * s.n_chan * (s.n_inputs / 16);

@@ -55,12 +55,14 @@ def test_items_per_channel_of_the_gram_layouts():
 
 def test_candidate_sets():
     p256 = autotune.packet_candidates(256)
-    assert {c["layout"] for c in p256} == {xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM}
+    assert {c["layout"] for c in p256} == {xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM, xe.XE_LAYOUT_FOLD_SPLIT}
+    assert {c["layout"] for c in autotune.packet_candidates(512)} == {xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM}
     assert {c["odd_pairs"] for c in p256} == {0, 1}
     p64 = autotune.packet_candidates(64)
     assert {c["layout"] for c in p64} == {xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE}
     f = autotune.frame_candidates(256, 100)
-    assert {c["layout"] for c in f} == {xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM, xe.XE_LAYOUT_FRAME_BLOCKS}
+    assert {c["layout"] for c in f} == {xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_GRAM, xe.XE_LAYOUT_FOLD_SPLIT,
+                                        xe.XE_LAYOUT_FRAME_BLOCKS}
     blk = [c for c in f if c["layout"] == xe.XE_LAYOUT_FRAME_BLOCKS]
     assert {c["pairs"] for c in blk} == {0, 60}       # 300 blocks: 5 rounds on 74 pairs, 60 pairs suffice
     # T % 4 != 0: only the 256-sample kernel reads such a frame
@@ -114,6 +116,10 @@ def test_tune_table_rejects_bad_entries():
     for bad in (dict(good, t_bucket=4000), dict(good, n_inputs=250), dict(good, layout=9), dict(good, mode=2),
                 dict(good, k_flush=100), dict(good, odd_pairs=2),
                 dict(good, layout=xe.XE_LAYOUT_FRAME_BLOCKS)):           # the 256-sample kernel: frames only
+        with pytest.raises(xe.XeError) as e:
+            xe.xe_tune_table_set([bad])
+        assert e.value.status == xe.XE_EINVAL
+    for bad in (dict(good, layout=7), dict(good, layout=-1)):
         with pytest.raises(xe.XeError) as e:
             xe.xe_tune_table_set([bad])
         assert e.value.status == xe.XE_EINVAL

@@ -26,7 +26,7 @@ from tests import xe_cuda as X
 pytestmark = pytest.mark.gpu
 
 GRAM_LAYOUTS = [xe.XE_LAYOUT_GRAM, xe.XE_LAYOUT_GRAM_TWIN, xe.XE_LAYOUT_GRAM_WIDE]
-ROW_LAYOUTS = [xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_FOLD] + GRAM_LAYOUTS
+ROW_LAYOUTS = [xe.XE_LAYOUT_AUTO, xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_FOLD_SPLIT] + GRAM_LAYOUTS
 
 
 @contextlib.contextmanager
@@ -77,7 +77,7 @@ def _packets(pk, seq0, gps, N, F, T, vis=None, accumulate=False):
     return vis
 
 
-@pytest.mark.parametrize("layout", [xe.XE_LAYOUT_FOLD] + GRAM_LAYOUTS)
+@pytest.mark.parametrize("layout", [xe.XE_LAYOUT_FOLD, xe.XE_LAYOUT_FOLD_SPLIT] + GRAM_LAYOUTS)
 @pytest.mark.parametrize("N,F,T,pairs", [
     (144, 8, 388, 2),         # one super-block, a half one (16 inputs) after it
     (256, 16, 516, 3),        # one whole super-block per channel; ragged time tail
@@ -120,6 +120,34 @@ def test_frame_layouts_accumulate(layout):
         X.correlate(a, vis, accumulate=True)
         X.correlate(b, vis, accumulate=True)
     np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), start + va + vb)
+
+
+@pytest.mark.parametrize("N,F,T,pairs", [(256, 13, 1028, 5), (144, 3, 260, 7), (256, 64, 516, 0), (192, 1, 132, 3),
+                                         (256, 2, 4, 5)])
+@pytest.mark.parametrize("accumulate", [False, True])
+def test_balanced_split_matches_oracle(N, F, T, pairs, accumulate):
+    """Fold items split evenly over the CTA pairs (pieces of consecutive channels, added in L2): the
+    channel x stage range cut at arbitrary stages, more pairs than stages, and a call that does not
+    accumulate writing over stale values. Frame and packet mode."""
+    fr, want = _frame_case(N, F, T)
+    start = np.random.default_rng(N + F).integers(-99, 99, want.shape)
+    with tuned([entry(N, T, xe.XE_TUNE_FRAMES, xe.XE_LAYOUT_FOLD_SPLIT, pairs=pairs)]):
+        vis = X.dev(start.astype(np.int32))
+        X.correlate(fr, vis, accumulate=accumulate)
+    np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want + (start if accumulate else 0))
+    if F % 8 == 0:
+        pk = synth.packetize(fr, 0, 1)
+        with tuned([entry(N, T, xe.XE_TUNE_PACKETS, xe.XE_LAYOUT_FOLD_SPLIT, pairs=pairs)]):
+            vis = _packets(pk, 0, 1, N, F, T, vis=X.dev(start.astype(np.int32)), accumulate=accumulate)
+        np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want + (start if accumulate else 0))
+
+
+def test_auto_splits_a_ragged_last_round():
+    """Without a table entry, 64 channels of 256 inputs (configuration 2's shape, shorter) on all
+    resident pairs take the balanced split; the result is the oracle's either way."""
+    fr, want = _frame_case(256, 64, 516)
+    vis = X.correlate(fr)
+    np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want)
 
 
 def test_frame_time_not_whole_slots_takes_the_256_sample_kernel():
