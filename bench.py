@@ -408,7 +408,7 @@ def run_xe(args):
 
     # the autotuner picks the pair engine's layout and launch shape for the calls this run makes
     from paper_1503_06189_b300 import autotune
-    table = autotune.Table(None)
+    table = autotune.Table(args.tune_cache)
     table.tune_packets(N, G * T)
     if G > 1:
         table.tune_packets(N, T)
@@ -806,7 +806,7 @@ def run_config(args):
     stream = torch.cuda.Stream(device=dev)
     # the autotuner picks the pair engine's kernel, layout and launch shape per (N, T-bucket) of the jobs
     from paper_1503_06189_b300 import autotune
-    table = autotune.Table(None)
+    table = autotune.Table(args.tune_cache)
     for N, F, T in shapes:
         table.tune_frames(N, T)
     table.install()
@@ -944,6 +944,9 @@ def main():
                          "stays in tensor memory across them)")
     ap.add_argument("--impl", choices=["xe", "reference"], default="xe")
     ap.add_argument("--no-serving", action="store_true", help="skip the configuration-5 serving run")
+    ap.add_argument("--tune-cache", default=None,
+                    help="JSON file of the autotuner's entries: read if it exists, written after tuning (a profiled "
+                         "run then launches what the plain run chose)")
     ap.add_argument("--config", type=int, choices=[1, 2, 3, 4, 6], default=3,
                     help="3: the full-band integration (default); 1, 2, 4: the other workloads; 6: N=2048 per server")
     args = ap.parse_args()

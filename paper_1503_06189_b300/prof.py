@@ -36,6 +36,8 @@ def main(argv=None):
                     help="packets: keep arrival (sequence-major) order or sort them group-major")
     ap.add_argument("--align", action="store_true",
                     help="packets: re-lay the packets at a 128-byte multiple stride with 128-byte aligned payloads")
+    ap.add_argument("--zero-copy-only", action="store_true",
+                    help="packets: time xe_correlate_packets only (no assembled frame is allocated)")
     ap.add_argument("--spread", type=int, default=64, help="shift: delays drawn from 0 .. spread samples")
     ap.add_argument("--uniform", action="store_true", help="shift: one delay per block of 16 inputs")
     a = ap.parse_args(argv)
@@ -80,6 +82,8 @@ def main(argv=None):
         del frame
         keep = torch.rand(pk.shape[0], generator=g, device=dev) >= 0.001
         pk = pk[keep].contiguous()
+        del keep
+        torch.cuda.empty_cache()                                # only the packets stay on the device
         if a.order == "group":                                  # all slots of a group together
             hdr = pk[:, :16].contiguous().view(torch.int32)
             key = (hdr[:, 0] & 0xFFFF).to(torch.int64) * (1 << 32) + hdr[:, 2].to(torch.int64)
@@ -95,9 +99,10 @@ def main(argv=None):
         lost = torch.zeros(F, dtype=torch.int32, device=dev)
         stats = torch.zeros(5, dtype=torch.int32, device=dev)
         ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device=dev)
-        out = torch.empty((T, F, N), dtype=torch.uint8, device=dev)
-        wsa = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
-        wsc = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
+        if not a.zero_copy_only:
+            out = torch.empty((T, F, N), dtype=torch.uint8, device=dev)
+            wsa = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
+            wsc = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
 
         def zero_copy():
             xe.xe_correlate_packets(pk, pk.shape[0], pk.shape[1], 0, 1, s, vis, a.accumulate, filled, lost, stats, ws)
@@ -107,7 +112,8 @@ def main(argv=None):
             xe.xe_correlate(out, s, vis, a.accumulate, wsc)
 
         cmac = F * P * T
-        for name, fn in (("zero-copy", zero_copy), ("two-step", two_step)):
+        runs = (("zero-copy", zero_copy),) + (() if a.zero_copy_only else (("two-step", two_step),))
+        for name, fn in runs:
             evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.iters)]
             for e0, e1 in evs:
                 e0.record()
