@@ -253,7 +253,10 @@ typedef struct {
     int32_t t_bucket;   /* T bucket: power of two >= 128 */
     int32_t mode;       /* XE_TUNE_PACKETS or XE_TUNE_FRAMES */
     int32_t layout;     /* XE_LAYOUT_* (XE_LAYOUT_FRAME_BLOCKS: frame mode only) */
-    int32_t pairs;      /* CTA pairs per launch, 0 = as many as can be resident */
+    int32_t pairs;      /* CTA pairs per launch, 0 = as many as can be resident; a count that would
+                           add a round of work items at a launch's item count (the tuner measures
+                           at its own probe size) gives way to the fewest pairs that keep the
+                           rounds of a launch on all resident pairs */
     int32_t odd_pairs;  /* 1: an odd pair count, 0: as counted, -1: the layout's default (odd for Gram) */
     int32_t k_flush;    /* drain interval in samples, multiple of 128 up to 32768; 0 = default */
 } xe_tune_entry;

@@ -658,20 +658,33 @@ constexpr int kPairConvFwdWarp = 2;           // forwards converter completion, 
 constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
 constexpr int kPairEpiWarp0 = 4;
 constexpr int kPairConvWarp0 = kPairEpiWarp0 + kPairEpiWarps;
-// Converter shape per mode. A stage is kKt samples. Frame mode: 256-sample stages (half the
-// per-stage bookkeeping of 128: 0.80 against 0.81 ms per full-band frame), 16 converter warps (more
-// warps hide the sample loads: 0.81 against 0.88 ms), two rows per thread, three register buffers
-// (two stages in flight). Packet mode: 128-sample stages and 8 warps of two rows, whose 128
-// registers per thread hold four buffers — the gathers need three stages in flight (1.02 ms;
-// 256-sample stages spill there: 1.39 ms). kRows sample rows per thread and block, kRowStep apart.
+// Converter shape per mode. A stage is kKt samples; 16 converter warps in both kernels. Frame mode
+// (the 256-sample kernel): 256-sample stages (half the per-stage bookkeeping of 128: 0.80 against
+// 0.81 ms per full-band frame), two rows per thread, three register buffers (two stages in flight).
+// Packet mode (the 128-sample kernel): one row per thread and two buffers, one stage in flight.
+// Measured on the 8-frame full-band call shape (296 channels) and the one-frame call: 16 warps with
+// two buffers 1.12 / 0.587 ms, with three 1.12 / 0.622, with four 1.67 / 0.90; 8 warps of two rows
+// with four buffers 1.27 / 0.70, with three 1.22 / 0.65. The sample gathers in flight occupy L1,
+// which the 196 KB of shared memory leaves at 60 KB per SM, and more warps rather than more stages
+// in flight hide their latency. kRows sample rows per thread and block, kRowStep apart.
 template <bool kPackets>
 struct PairShape {
     static constexpr int kKt = kPackets ? kPairKtPackets : kPairKtFrame;
-    static constexpr int kConvWarps = kPackets ? 8 : 16;
+    static constexpr int kConvWarps = 16;
     static constexpr int kRows = kKt * 4 / (32 * kConvWarps);
     static constexpr int kRowStep = kKt / kRows;
-    static constexpr int kBufs = kPackets ? 4 : 3;
+    static constexpr int kBufs = kPackets ? 2 : 3;
     static constexpr int kThreads = 32 * (kPairConvWarp0 + kConvWarps);
+    // registers per thread: at launch (the __launch_bounds__ limit), and after the split between
+    // the role, epilogue and converter warpgroups, which hands out exactly the registers the
+    // launch allocates (the role warps need few, the epilogue more than the launch's 80)
+    static constexpr int kRegsLaunch = 65536 / kThreads / 8 * 8;
+    static constexpr int kRegsRoles = 48;
+    static constexpr int kRegsEpi = 112;
+    static constexpr int kRegsConv = (kRegsLaunch * kThreads - 128 * (kRegsRoles + kRegsEpi)) / (32 * kConvWarps) / 8 * 8;
+    static_assert(kRegsConv >= 24 && kRegsConv <= 256, "a warpgroup holds 24 to 256 registers per thread");
+    static_assert(128 * kRegsRoles + 128 * kRegsEpi + 32 * kConvWarps * kRegsConv <= kRegsLaunch * kThreads,
+                  "the register split fits the launch's registers");
     static_assert(kRows * 32 * kConvWarps == kKt * 4, "conversion tasks divide evenly");
     static_assert(kRowStep % 8 == 0, "a thread's rows share their 128-byte swizzle phase");
 };
@@ -1107,6 +1120,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         }
     };
 
+    // Roles by warpgroup, with the registers split between them: the role warps (0-3) need few,
+    // the epilogue (4-7) more than the launch's 80, and the converters (8-23) keep 80:
+    // 128 x 48 + 128 x 112 + 512 x 80 = 768 x 80. Each warpgroup's whole role code follows its
+    // split, so the compiler sizes that code for it (the epilogue's spills go away).
+    if (warp < kPairEpiWarp0) {
+    dev::setmaxnreg_dec<S::kRegsRoles>();
     if (warp == kPairConvFwdWarp) {
         if (!kPackets && lane == 0) {
             // ---------------------------------------------------------------- converter forwarder
@@ -1228,8 +1247,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             dev::tc_commit_pair_multicast(done, 1);
             dev::mbar_wait(done, 0, p.limit_ns);
         }
-    } else if (warp >= kPairEpiWarp0 && warp < kPairConvWarp0) {
+    }
+    } else if (warp < kPairConvWarp0) {
         // -------------------------------------------------------------------- epilogue (both CTAs)
+        if constexpr (S::kRegsEpi > S::kRegsLaunch) dev::setmaxnreg_inc<S::kRegsEpi>();
+        else if constexpr (S::kRegsEpi < S::kRegsLaunch) dev::setmaxnreg_dec<S::kRegsEpi>();
         using O = Order<true>;
         constexpr int kPerQuarter = kPairEpiWarps / 4;
         constexpr float kMagic = 12582912.0f;               // 1.5 * 2^23
@@ -1238,7 +1260,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         const int half = (warp - kPairEpiWarp0) >> 2;
         const int m = q * 32 + lane;
         const bool im_row = O::comp_of(m) != 0;
-        const uint32_t partner = rank ^ 1u;
         uint32_t acc = 0, acc_ph = 0, x_ph = 0;
         bool ok = true;
         // Fold items synchronise the four epilogue warps with a named barrier, so every warp walks
@@ -1474,8 +1495,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
                 acc ^= 1u;
             }
         }
-    } else if (warp >= kPairConvWarp0) {
+    } else {
         // -------------------------------------------------------------------- converters (both CTAs)
+        if constexpr (S::kRegsConv > S::kRegsLaunch) dev::setmaxnreg_inc<S::kRegsConv>();
+        else if constexpr (S::kRegsConv < S::kRegsLaunch) dev::setmaxnreg_dec<S::kRegsConv>();
         // thread ctid converts inputs 16c .. 16c + 15 of samples t_row + r kRowStep (t_row = ctid / 4)
         // of each block: 16 packed bytes in, 32 E5M2 codes out into the two 16-byte chunks 2c and
         // 2c + 1 of those operand rows (128-byte swizzle; all of a thread's rows share its phase). A
@@ -1591,26 +1614,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
             return true;
         };
-        static_assert(S::kBufs == 3 || S::kBufs == 4, "the rotations below use three or four buffers");
-        Buf x, y, z, w;
+        static_assert(S::kBufs == 2 || S::kBufs == 3, "the rotations below use two or three buffers");
+        Buf x, y, z;
 #pragma unroll
-        for (int q = 0; q < kOwn; ++q) x.own[q] = y.own[q] = z.own[q] = w.own[q] = kNoPacket;
-        if constexpr (S::kBufs == 4) {
-            next_owners(x);                           // stages 0, 1, 2, 3
+        for (int q = 0; q < kOwn; ++q) x.own[q] = y.own[q] = z.own[q] = kNoPacket;
+        if constexpr (S::kBufs == 2) {
+            next_owners(x);                           // stages 0, 1
             next_owners(y);
-            next_owners(z);
-            next_owners(w);
             issue(x);
-            next_owners(x);                           // stage 4
-            issue(y);
-            next_owners(y);                           // stage 5
-            issue(z);
-            next_owners(z);                           // stage 6
+            next_owners(x);                           // stage 2
             for (;;) {
-                if (!step(w, x)) break;
+                if (!step(y, x)) break;
                 if (!step(x, y)) break;
-                if (!step(y, z)) break;
-                if (!step(z, w)) break;
             }
         } else {
             next_owners(x);                           // stages 0, 1, 2
@@ -1765,12 +1780,19 @@ static int launch_gemm(const Params &hp, int ctas, int smem, cudaStream_t st) {
 // Pair engine: as many 2-CTA clusters as can be resident at once (each CTA fills an SM), one per
 // work item at most, at most n_ctas / 2 if n_ctas > 0.
 template <bool kPackets>
-static int pair_count(int items, int n_ctas, bool odd_pairs, int *out) {
+static int pair_count(int items, int n_ctas, bool odd_pairs, bool keep_rounds, int *out) {
     static int max_pairs[64] = {};
     int dev = 0;
     XE_TRY_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return XE_EINVAL;
     if (!max_pairs[dev]) {
+        {
+            // the kernel's register split (setmaxnreg) hands back exactly what it takes from the
+            // registers a launch allocates; with any other allocation its increase could not be met
+            cudaFuncAttributes fa{};
+            XE_TRY_CUDA(cudaFuncGetAttributes(&fa, correlate_pair_kernel<kPackets>));
+            if (fa.numRegs != PairShape<kPackets>::kRegsLaunch) return XE_ECUDA;
+        }
         XE_TRY_CUDA(cudaFuncSetAttribute(correlate_pair_kernel<kPackets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemMax));
         cudaLaunchConfig_t cfg = {};
@@ -1789,7 +1811,13 @@ static int pair_count(int items, int n_ctas, bool odd_pairs, int *out) {
         max_pairs[dev] = std::max(1, n);
     }
     int pairs = std::min(items, max_pairs[dev]);
+    const int rounds_all = (items + pairs - 1) / pairs;
     if (n_ctas > 0) pairs = std::max(1, std::min(pairs, n_ctas / 2));
+    // a count from the tuning table was measured at the autotuner's probe size: where it adds a
+    // round of work items at this launch's count, the launch takes the fewest pairs that keep the
+    // rounds of a launch on all pairs instead (N = 2048, 64 channels: 68 pairs would run 128 rounds
+    // of Gram blocks, 74 run 118)
+    if (keep_rounds && (items + pairs - 1) / pairs > rounds_all) pairs = (items + rounds_all - 1) / rounds_all;
     // the packet-mode Gram layout interleaves doubles and singles channel by channel: an odd pair
     // count makes every pair alternate between the two kinds (fold items are all alike). One pair
     // fewer is not taken where it adds a round of work items: a full-band call of 1,024 fold items
@@ -1803,9 +1831,10 @@ static int pair_count(int items, int n_ctas, bool odd_pairs, int *out) {
 }
 
 template <bool kPackets>
-static int launch_pair(const Params &hp, int items, int n_ctas, int smem, bool odd_pairs, cudaStream_t st) {
+static int launch_pair(const Params &hp, int items, int n_ctas, int smem, bool odd_pairs, bool keep_rounds,
+                       cudaStream_t st) {
     int pairs = 0;
-    if (int e = pair_count<kPackets>(items, n_ctas, odd_pairs, &pairs)) return e;
+    if (int e = pair_count<kPackets>(items, n_ctas, odd_pairs, keep_rounds, &pairs)) return e;
     correlate_pair_kernel<kPackets><<<2 * pairs, PairShape<kPackets>::kThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
@@ -1841,6 +1870,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     bool has_ent[XE_MAX_JOBS] = {};
     xe_tune_entry launch_ent{};
     bool has_launch_ent = false;
+    bool pairs_from_table = false;
     if (engine == kFusedPair) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         double best = -1.0;
@@ -1856,7 +1886,10 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     }
     if (has_launch_ent) {
         if (!(tune_in && tune_in->k_flush) && launch_ent.k_flush) tune.k_flush = launch_ent.k_flush;
-        if (!(tune_in && tune_in->n_ctas) && launch_ent.pairs) tune.n_ctas = 2 * launch_ent.pairs;
+        if (!(tune_in && tune_in->n_ctas) && launch_ent.pairs) {
+            tune.n_ctas = 2 * launch_ent.pairs;
+            pairs_from_table = true;
+        }
     }
     // The pair engine's 128-sample kernel (the packet-mode kernel) also reads assembled frames, in
     // 4-sample slots (whole slots only: T % 4 == 0), with every item layout. A frame launch takes it
@@ -2053,7 +2086,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         // the Gram layout's doubles and singles alternate best on an odd pair count; fold items are alike
         bool odd = rows128 && !all_fold;
         if (has_launch_ent && launch_ent.odd_pairs >= 0) odd = launch_ent.odd_pairs == 1;
-        if (!rows128) return launch_pair<false>(hp, items, tune.n_ctas, smem, odd, st);
+        if (!rows128) return launch_pair<false>(hp, items, tune.n_ctas, smem, odd, pairs_from_table, st);
         // Balanced split: a launch of one job whose channels are one fold item each (129-256
         // inputs) hands every pair an equal share of the job's channel x stage range, as pieces of
         // consecutive channels, when whole items would leave more than a tenth of the last round's
@@ -2063,7 +2096,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
         Job &d0 = hp.jobs[0];
         if (nj == 1 && d0.fold && d0.nb == 2) {
             int pairs = 0;
-            if (int e = pair_count<true>(items, tune.n_ctas, false, &pairs)) return e;
+            if (int e = pair_count<true>(items, tune.n_ctas, false, pairs_from_table, &pairs)) return e;
             const int rounds = (items + pairs - 1) / pairs;
             const bool ragged = (double)items < 0.9 * (double)rounds * (double)pairs;
             if (job_layout[0] == XE_LAYOUT_FOLD_SPLIT || ragged) {
@@ -2077,10 +2110,10 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
                     XE_TRY_CUDA(cudaMemsetAsync(d0.vis, 0, (size_t)d0.n_chan * npairs(d0.n_inputs) * 8, st));
                     d0.accumulate = 1;
                 }
-                return launch_pair<true>(hp, items, 2 * pairs, smem, false, st);
+                return launch_pair<true>(hp, items, 2 * pairs, smem, false, false, st);
             }
         }
-        return launch_pair<true>(hp, items, tune.n_ctas, smem, odd, st);
+        return launch_pair<true>(hp, items, tune.n_ctas, smem, odd, pairs_from_table, st);
     }
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
     switch (engine) {

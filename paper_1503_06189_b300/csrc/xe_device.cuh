@@ -220,6 +220,17 @@ __device__ __forceinline__ void tmem_alloc_pair(uint32_t *slot, uint32_t ncols) 
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
                  ::"r"(smem_u32(slot)), "r"(ncols) : "memory");
 }
+// Register split between warpgroups (all four warps of a warpgroup execute it): dec hands registers
+// back to the CTA's pool, inc waits until the pool holds enough. The counts must add up to at most
+// the launch's registers per thread x threads, which the host checks before the launch.
+template <uint32_t kRegs>
+__device__ __forceinline__ void setmaxnreg_dec() {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegs));
+}
+template <uint32_t kRegs>
+__device__ __forceinline__ void setmaxnreg_inc() {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegs));
+}
 __device__ __forceinline__ void tmem_relinquish_pair() {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
 }
