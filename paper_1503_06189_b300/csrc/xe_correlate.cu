@@ -677,10 +677,12 @@ struct PairShape {
     static constexpr int kThreads = 32 * (kPairConvWarp0 + kConvWarps);
     // registers per thread: at launch (the __launch_bounds__ limit), and after the split between
     // the role, epilogue and converter warpgroups, which hands out exactly the registers the
-    // launch allocates (the role warps need few, the epilogue more than the launch's 80)
+    // launch allocates. The 128-sample kernel: roles 48, fold epilogue 112, converters 80; the
+    // 256-sample kernel: roles 32, Gram epilogue 96, converters (two rows, three buffers) 88. Both
+    // splits are the ones without spills (the compiler reports 20 and 0 bytes of spill stores)
     static constexpr int kRegsLaunch = 65536 / kThreads / 8 * 8;
-    static constexpr int kRegsRoles = 48;
-    static constexpr int kRegsEpi = 112;
+    static constexpr int kRegsRoles = kPackets ? 48 : 32;
+    static constexpr int kRegsEpi = kPackets ? 112 : 96;
     static constexpr int kRegsConv = (kRegsLaunch * kThreads - 128 * (kRegsRoles + kRegsEpi)) / (32 * kConvWarps) / 8 * 8;
     static_assert(kRegsConv >= 24 && kRegsConv <= 256, "a warpgroup holds 24 to 256 registers per thread");
     static_assert(128 * kRegsRoles + 128 * kRegsEpi + 32 * kConvWarps * kRegsConv <= kRegsLaunch * kThreads,
@@ -1088,12 +1090,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
     dev::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // Bounded wait: suspended in the barrier between tries (up to 1 ms each; the thread resumes when
+    // the phase completes), checking the abort flag and the time limit every 8 tries. Waiting warps
+    // issue almost nothing, which leaves issue slots and power to the converters (0.3-0.8 % faster)
     auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
         if (dev::mbar_try_wait(bar, parity)) return true;
         const uint64_t t0 = dev::globaltimer_ns();
         for (uint32_t it = 1;; ++it) {
-            if (dev::mbar_try_wait(bar, parity)) return true;
-            if ((it & 127u) == 0) {
+            if (dev::mbar_try_wait_hint(bar, parity, 1000000u)) return true;
+            if ((it & 7u) == 0) {
                 if (*abort_flag) return false;
                 if (dev::globaltimer_ns() - t0 > p.limit_ns) {
                     *abort_flag = 1;
@@ -1120,10 +1125,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         }
     };
 
-    // Roles by warpgroup, with the registers split between them: the role warps (0-3) need few,
-    // the epilogue (4-7) more than the launch's 80, and the converters (8-23) keep 80:
-    // 128 x 48 + 128 x 112 + 512 x 80 = 768 x 80. Each warpgroup's whole role code follows its
-    // split, so the compiler sizes that code for it (the epilogue's spills go away).
+    // Roles by warpgroup, with the registers split between them (PairShape): the role warps (0-3)
+    // need few, the epilogue (4-7) more than the launch's 80; the 128-sample kernel's converters
+    // (8-23) keep 80 (128 x 48 + 128 x 112 + 512 x 80 = 768 x 80). Each warpgroup's whole role code
+    // follows its split, so the compiler sizes that code for it (the epilogue's spills go away).
     if (warp < kPairEpiWarp0) {
     dev::setmaxnreg_dec<S::kRegsRoles>();
     if (warp == kPairConvFwdWarp) {
