@@ -142,10 +142,12 @@ def test_balanced_split_matches_oracle(N, F, T, pairs, accumulate):
         np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want + (start if accumulate else 0))
 
 
-def test_auto_splits_a_ragged_last_round():
-    """Without a table entry, 64 channels of 256 inputs (configuration 2's shape, shorter) on all
-    resident pairs take the balanced split; the result is the oracle's either way."""
-    fr, want = _frame_case(256, 64, 516)
+@pytest.mark.parametrize("F", [64, 96])
+def test_auto_splits_a_ragged_last_round(F):
+    """Without a table entry, 96 channels of 256 inputs (two rounds of fold items on 74 pairs, the
+    second a third full) take the balanced split, and 64 channels (configuration 2's shape, shorter:
+    one round) one pair per channel; the result is the oracle's either way."""
+    fr, want = _frame_case(256, F, 516)
     vis = X.correlate(fr)
     np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want)
 
