@@ -42,6 +42,8 @@ extern "C" {
 /* Largest time-sample count whose int32 sums cannot overflow: |re V| <= 128 per sample, so
  * 128 * (2^24 - 1) = 2^31 - 128 is the largest reachable value. */
 #define XE_MAX_TIME 16777215
+/* Largest input count N of a correlation (N is a multiple of 16 from 16 up). */
+#define XE_MAX_INPUTS 4096
 
 typedef struct {
     int32_t n_inputs;   /* N: inputs (antenna feeds x polarisations), multiple of 16 */
@@ -314,6 +316,25 @@ int xe_correlate_packets(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stri
                          int32_t groups_per_stream, xe_shape s, int32_t *vis, int accumulate,
                          uint8_t *filled, uint32_t *lost, uint32_t *stats, void *ws, size_t ws_bytes,
                          void *stream);
+
+/*
+ * xe_correlate_packets with the time shift of Fig. 4's caption applied while the samples are read
+ * (no shifted frame is written, no extra pass over the data). The result is exactly that of
+ * xe_assemble, then xe_time_shift with `delays`, then xe_correlate: input n of every channel is
+ * read delays[n] samples late, and the first delays[n] samples of the frame read as zeros (no
+ * data). The shift is applied per block of 16 inputs, the unit one converter thread reads: the 16
+ * inputs 16b .. 16b + 15 must share one delay (inputs fed through one cable or digitiser board).
+ *   delays      HOST, int32 [N], 0 <= delays[n] <= T, delays[16b + k] == delays[16b] (read during
+ *               the call; the values go into the launch's parameters, so a captured graph keeps them)
+ *   others      as xe_correlate_packets (same workspace size).
+ * Add the samples without data to the normalisation's counters with xe_time_shift_counts.
+ * Errors: those of xe_correlate_packets; XE_EINVAL for a delay out of range or differing within a
+ * block of 16 inputs.
+ */
+int xe_correlate_packets_shifted(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
+                                 int32_t groups_per_stream, xe_shape s, const int32_t *delays, int32_t *vis,
+                                 int accumulate, uint8_t *filled, uint32_t *lost, uint32_t *stats, void *ws,
+                                 size_t ws_bytes, void *stream);
 
 /*
  * F-engine flags of one frame (Sec. II-C: the F-engine flags samples of individual inputs,

@@ -32,7 +32,8 @@ EXPORTED = [
     "xe_assemble_workspace_size", "xe_assemble", "xe_assemble_noalloc", "xe_unpack", "xe_correlate_workspace_size",
     "xe_correlate", "xe_correlate_batched_workspace_size", "xe_correlate_batched", "xe_tune_table_set",
     "xe_tune_table_get",
-    "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_flag_counts_workspace_size",
+    "xe_correlate_packets_workspace_size", "xe_correlate_packets", "xe_correlate_packets_shifted",
+    "xe_flag_counts_workspace_size",
     "xe_flag_counts", "xe_normalize", "xe_probe_mma_legacy", "xe_time_shift", "xe_time_shift_counts",
     "xe_stream_create", "xe_stream_submit", "xe_stream_submit_device", "xe_stream_flush", "xe_stream_poll", "xe_stream_release",
     "xe_stream_stats", "xe_stream_destroy",
@@ -131,6 +132,8 @@ def _load():
     L.xe_correlate_packets_workspace_size.restype = sz
     L.xe_correlate_packets_workspace_size.argtypes = [Shape]
     L.xe_correlate_packets.argtypes = [vp, u32, u32, u64, i32, Shape, vp, ctypes.c_int, vp, vp, vp, vp, sz, vp]
+    L.xe_correlate_packets_shifted.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, ctypes.c_int, vp, vp, vp, vp,
+                                               sz, vp]
     L.xe_flag_counts_workspace_size.restype = sz
     L.xe_flag_counts_workspace_size.argtypes = [Shape]
     L.xe_flag_counts.argtypes = [vp, u32, u32, u64, i32, Shape, vp, vp, vp, sz, vp]
@@ -349,6 +352,17 @@ def xe_correlate_packets(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_p
     _check(_L.xe_correlate_packets(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape, _dptr(vis),
                                    1 if accumulate else 0, _dptr(filled), _dptr(lost), _dptr(stats), _dptr(ws),
                                    _nbytes(ws), _stream(stream)), "xe_correlate_packets")
+
+
+def xe_correlate_packets_shifted(pkts, n_pkts: int, pkt_stride: int, seq0: int, groups_per_stream: int,
+                                 shape: Shape, delays, vis, accumulate: bool, filled, lost, stats, ws, stream=None):
+    """xe_correlate_packets with input n read delays[n] samples late (host sequence of N ints, equal within
+    each block of 16 inputs): the result of xe_assemble, xe_time_shift and xe_correlate, in one pass."""
+    d = _host_delays(delays, shape.n_inputs)
+    _check(_L.xe_correlate_packets_shifted(_dptr(pkts), n_pkts, pkt_stride, seq0, groups_per_stream, shape,
+                                           d.ctypes.data, _dptr(vis), 1 if accumulate else 0, _dptr(filled),
+                                           _dptr(lost), _dptr(stats), _dptr(ws), _nbytes(ws), _stream(stream)),
+           "xe_correlate_packets_shifted")
 
 
 # ----------------------------------------------------------------------------- time shift

@@ -90,6 +90,10 @@ struct Params {
     // [q split_u, (q + 1) split_u) of the job's channel-major F x k_tiles stages, as up to
     // split_items items (pieces of consecutive channels); 0 = off
     int32_t split_u, split_pairs, split_items;
+    // time-shifted packet calls (the kShift kernel, one job): the delay in samples of each block of
+    // 16 inputs (inputs 16 b .. 16 b + 15 share delay16[b]); sample t of input n is read from row
+    // t - delay16[n / 16] of the frame, zero before the frame's start
+    int32_t delay16[XE_MAX_INPUTS / 16];
     int *status;
     int *counter;            // work-item counter, zero at launch
     uint64_t limit_ns;
@@ -896,9 +900,10 @@ constexpr uint32_t kNoPacket = 0xFFFFFFFFu;
 // f % 8) N + column; a lost packet (o = ~0u) reads as zeros, as in an assembled frame. The
 // kKt / 4 slots of a stage are looked up by coalesced loads, one per 32 slots and warp (lane l:
 // slots l, l + 32, ...), and each thread takes the packets of its rows from those lanes by shfl.
-template <bool kPackets>
+template <bool kPackets, bool kShift = false>
 struct PairLoader {
     using S = PairShape<kPackets>;
+    static_assert(!kShift || (kPackets && S::kRows == 1), "the shifted reads run in the packet kernel");
     static constexpr int kOwn = S::kKt / 4 / 32;          // owner loads per lane and stage
     static constexpr int kOwnMax = kPackets ? 2 * kOwn : 1;   // a wide stage looks up twice as many
     int g, kt, k_tiles, nblk, t_left;         // t_left = T - (kt * S::kKt + t_row)
@@ -911,6 +916,11 @@ struct PairLoader {
     uintptr_t own;
     int s_left;                               // T / 4 - (kt * S::kKt / 4 + lane)
     int64_t pstride;
+    // time-shifted packets: the source slots of this thread's A and B rows in the current stage
+    // (below 0 or from T / 4 on: outside the frame, read as zeros), the slots of the rows themselves
+    // (from T / 4 on: past the frame's end, zeros too), and the owner entries of its channel group
+    int sa, sb, ua, ub, q_slots;
+    const uint32_t *orow;
 
     __device__ __forceinline__ void begin_item(const Params &p, uint32_t rank, int t_row, int c) {
         const PairItem it = decode_pair_item<kPackets>(p, g);
@@ -943,7 +953,22 @@ struct PairLoader {
         const uint8_t *base;
         if constexpr (kPackets) {
             const int Q = jb.n_time / 4, lane = threadIdx.x & 31;
-            if (!p.frame_rows) {
+            if constexpr (kShift) {
+                // row t of the shifted frame is row t - d of the frame: slot (t - d) / 4 (floor) and
+                // row (t - d) mod 4 of that packet; a wide stage's B rows lie kKt samples further on
+                const int da = va ? p.delay16[ca >> 4] : 0, db = vb ? p.delay16[cb >> 4] : 0;
+                const int ta = t_row - da, tb = t_row - db + (wide ? S::kKt : 0);
+                sa = ta >> 2;
+                sb = tb >> 2;
+                ua = t_row >> 2;
+                ub = (t_row + (wide ? S::kKt : 0)) >> 2;
+                q_slots = Q;
+                orow = jb.owner + (size_t)(it.f / 8) * Q;
+                pstride = jb.pkt_stride;
+                pa = jb.pkts + 16 + ((size_t)(ta & 3) * 8 + it.f % 8) * N + ca;
+                pb = jb.pkts + 16 + ((size_t)(tb & 3) * 8 + it.f % 8) * N + cb + (twin ? N : 0);
+                base = nullptr;
+            } else if (!p.frame_rows) {
                 base = jb.pkts + 16 + ((size_t)(t_row & 3) * 8 + it.f % 8) * N;
                 own = reinterpret_cast<uintptr_t>(jb.owner + (size_t)(it.f / 8) * Q + lane);
                 pstride = jb.pkt_stride;
@@ -960,12 +985,21 @@ struct PairLoader {
             step = (int64_t)S::kKt * F * N;
             rstep = (int64_t)S::kRowStep * F * N;
         }
-        pa = base + ca;
-        pb = base + cb + (twin ? N : 0);      // a twin's B block: channel f + 1, N bytes on
+        if (!kShift) {
+            pa = base + ca;
+            pb = base + cb + (twin ? N : 0);  // a twin's B block: channel f + 1, N bytes on
+        }
         if constexpr (kPackets) {             // (the balanced split runs in this kernel only)
             if (it.kt0) {                     // a piece of a split integration starts kt0 stages in
-                own += (uintptr_t)it.kt0 * S::kKt;
-                s_left -= it.kt0 * (S::kKt / 4);
+                if constexpr (kShift) {
+                    sa += it.kt0 * (S::kKt / 4);
+                    sb += it.kt0 * (S::kKt / 4);
+                    ua += it.kt0 * (S::kKt / 4);
+                    ub += it.kt0 * (S::kKt / 4);
+                } else {
+                    own += (uintptr_t)it.kt0 * S::kKt;
+                    s_left -= it.kt0 * (S::kKt / 4);
+                }
             }
         }
     }
@@ -976,7 +1010,12 @@ struct PairLoader {
     __device__ __forceinline__ bool valid(const Params &p) const { return g < p.n_items; }
     __device__ __forceinline__ void next(const Params &p, int n_pairs, uint32_t rank, int t_row, int c) {
         t_left -= S::kKt;
-        if constexpr (kPackets) {
+        if constexpr (kShift) {
+            sa += (wide ? 2 : 1) * (S::kKt / 4);
+            sb += (wide ? 2 : 1) * (S::kKt / 4);
+            ua += (wide ? 2 : 1) * (S::kKt / 4);
+            ub += (wide ? 2 : 1) * (S::kKt / 4);
+        } else if constexpr (kPackets) {
             own += (wide ? 2 : 1) * S::kKt;       // kKt / 4 slots of 4 bytes
             s_left -= (wide ? 2 : 1) * (S::kKt / 4);
         } else {
@@ -989,14 +1028,21 @@ struct PairLoader {
     }
     // packets: the packets of slots lane, lane + 32, ... of the current stage (a wide stage: then
     // those of slots kKt / 4 + lane, ... in o[kOwn ..])
+    // Time-shifted packets: o[0] / o[1] the packets of this thread's A / B row of the stage.
     __device__ __forceinline__ void owners(const Params &p, uint32_t (&o)[kOwnMax]) const {
+        if constexpr (kShift) {
+            o[0] = o[1] = kNoPacket;
+            if (sa >= 0 && sa < q_slots && ua < q_slots) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[0]) : "l"(orow + sa));
+            if (sb >= 0 && sb < q_slots && ub < q_slots) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[1]) : "l"(orow + sb));
+        } else {
 #pragma unroll
-        for (int q = 0; q < kOwnMax; ++q) {
-            o[q] = kNoPacket;
-            if constexpr (kPackets) {
-                if ((q < kOwn || wide) && s_left > 32 * q) {
-                    if (!p.frame_rows) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[q]) : "l"(own + 128 * q));
-                    else o[q] = (uint32_t)(own / 4) + 32 * q;           // frame rows: the slot itself
+            for (int q = 0; q < kOwnMax; ++q) {
+                o[q] = kNoPacket;
+                if constexpr (kPackets) {
+                    if ((q < kOwn || wide) && s_left > 32 * q) {
+                        if (!p.frame_rows) asm("ld.global.nc.u32 %0, [%1];" : "=r"(o[q]) : "l"(own + 128 * q));
+                        else o[q] = (uint32_t)(own / 4) + 32 * q;       // frame rows: the slot itself
+                    }
                 }
             }
         }
@@ -1022,7 +1068,7 @@ struct PairLoader {
     }
 };
 
-template <bool kPackets>
+template <bool kPackets, bool kShift = false>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>::kThreads, 1)
     correlate_pair_kernel(const __grid_constant__ Params p) {
     using S = PairShape<kPackets>;
@@ -1532,7 +1578,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             st16(row + kOpSlotBytes + dst, fa);
             st16(row + 2 * kOpSlotBytes + dst, fb);
         };
-        constexpr int kOwn = PairLoader<kPackets>::kOwnMax;
+        constexpr int kOwn = PairLoader<kPackets, kShift>::kOwnMax;
         struct Buf {
             uint4 a[S::kRows], b[S::kRows];
             uint32_t own[kOwn];                       // packets of the stage this buffer receives next
@@ -1542,7 +1588,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
         // in rotation (the loop is unrolled so that no buffer is copied); packet mode looks up a
         // stage's packets kBufs stages before its samples are loaded (right after the buffer that
         // will receive them issued its previous load)
-        PairLoader<kPackets> ld, ow;
+        PairLoader<kPackets, kShift> ld, ow;
         ld.start(p, pair, rank, t_row, c);
         ow = ld;
         auto next_owners = [&](Buf &b) {
@@ -1561,11 +1607,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
 #pragma unroll
             for (int r = 0; r < S::kRows; ++r) {
                 o[r] = ob[r] = 0;
-                if constexpr (kPackets) {
+                if constexpr (kShift) {
+                    o[r] = b.own[0];                  // this thread's own A and B row packets
+                    ob[r] = b.own[1];
+                } else if constexpr (kPackets) {
                     // slot (r kRowStep + t_row) / 4 of the stage: register (r kRowStep / 4) / 32,
                     // lane (r kRowStep / 4) % 32 + t_row / 4 (t_row / 4 < kRowStep / 4 <= 32); a wide
                     // stage's B rows: the same slot kKt / 4 further on (registers kOwn / 2 ..)
-                    constexpr int kHalf = PairLoader<kPackets>::kOwn;
+                    constexpr int kHalf = PairLoader<kPackets, kShift>::kOwn;
                     const int s0 = r * (S::kRowStep / 4);
                     o[r] = __shfl_sync(0xffffffffu, b.own[s0 / 32], s0 % 32 + (t_row >> 2));
                     ob[r] = o[r];
@@ -1784,7 +1833,7 @@ static int launch_gemm(const Params &hp, int ctas, int smem, cudaStream_t st) {
 
 // Pair engine: as many 2-CTA clusters as can be resident at once (each CTA fills an SM), one per
 // work item at most, at most n_ctas / 2 if n_ctas > 0.
-template <bool kPackets>
+template <bool kPackets, bool kShift = false>
 static int pair_count(int items, int n_ctas, bool odd_pairs, bool keep_rounds, int *out) {
     static int max_pairs[64] = {};
     int dev = 0;
@@ -1795,10 +1844,10 @@ static int pair_count(int items, int n_ctas, bool odd_pairs, bool keep_rounds, i
             // the kernel's register split (setmaxnreg) hands back exactly what it takes from the
             // registers a launch allocates; with any other allocation its increase could not be met
             cudaFuncAttributes fa{};
-            XE_TRY_CUDA(cudaFuncGetAttributes(&fa, correlate_pair_kernel<kPackets>));
+            XE_TRY_CUDA(cudaFuncGetAttributes(&fa, correlate_pair_kernel<kPackets, kShift>));
             if (fa.numRegs != PairShape<kPackets>::kRegsLaunch) return XE_ECUDA;
         }
-        XE_TRY_CUDA(cudaFuncSetAttribute(correlate_pair_kernel<kPackets>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        XE_TRY_CUDA(cudaFuncSetAttribute(correlate_pair_kernel<kPackets, kShift>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kSmemMax));
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
@@ -1812,7 +1861,7 @@ static int pair_count(int items, int n_ctas, bool odd_pairs, bool keep_rounds, i
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        XE_TRY_CUDA(cudaOccupancyMaxActiveClusters(&n, correlate_pair_kernel<kPackets>, &cfg));
+        XE_TRY_CUDA(cudaOccupancyMaxActiveClusters(&n, correlate_pair_kernel<kPackets, kShift>, &cfg));
         max_pairs[dev] = std::max(1, n);
     }
     int pairs = std::min(items, max_pairs[dev]);
@@ -1835,21 +1884,24 @@ static int pair_count(int items, int n_ctas, bool odd_pairs, bool keep_rounds, i
     return XE_OK;
 }
 
-template <bool kPackets>
+template <bool kPackets, bool kShift = false>
 static int launch_pair(const Params &hp, int items, int n_ctas, int smem, bool odd_pairs, bool keep_rounds,
                        cudaStream_t st) {
     int pairs = 0;
-    if (int e = pair_count<kPackets>(items, n_ctas, odd_pairs, keep_rounds, &pairs)) return e;
-    correlate_pair_kernel<kPackets><<<2 * pairs, PairShape<kPackets>::kThreads, smem, st>>>(hp);
+    if (int e = pair_count<kPackets, kShift>(items, n_ctas, odd_pairs, keep_rounds, &pairs)) return e;
+    correlate_pair_kernel<kPackets, kShift><<<2 * pairs, PairShape<kPackets>::kThreads, smem, st>>>(hp);
     XE_TRY_CUDA(cudaGetLastError());
     return XE_OK;
 }
 
 // pk (packet mode, pair engine only): job j reads its samples from the packets pk[j] through the
 // frame index pk[j].owner instead of from jobs[j].frame.
+// delay16 (packet mode, one job only): the delay of each block of 16 inputs, HOST [N / 16], read
+// here; the samples are read time-shifted (the kShift kernel).
 static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, void *ws, size_t ws_bytes,
-                       cudaStream_t st, const PacketSrc *pk) {
+                       cudaStream_t st, const PacketSrc *pk, const int32_t *delay16 = nullptr) {
     if (!jobs || n_jobs < 1 || n_jobs > XE_MAX_JOBS) return XE_EINVAL;
+    if (delay16 && (!pk || n_jobs != 1)) return XE_EINVAL;
     xe_tune tune;
     resolve_tune(tune_in, tune);
     if (int e = check_tune(tune)) return e;
@@ -1922,6 +1974,7 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
     static std::mutex mu;
     std::lock_guard<std::mutex> lock(mu);
     std::memset(&hp, 0, sizeof(hp));
+    if (delay16) std::memcpy(hp.delay16, delay16, sizeof(int32_t) * (size_t)(jobs[0].s.n_inputs / 16));
     uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
     int *counter = reinterpret_cast<int *>(base);
     uint8_t *ybase = base + kWsHeader;
@@ -2117,9 +2170,11 @@ static int run_batched(const xe_job *jobs, int n_jobs, const xe_tune *tune_in, v
                     XE_TRY_CUDA(cudaMemsetAsync(d0.vis, 0, (size_t)d0.n_chan * npairs(d0.n_inputs) * 8, st));
                     d0.accumulate = 1;
                 }
+                if (delay16) return launch_pair<true, true>(hp, items, 2 * pairs, smem, false, false, st);
                 return launch_pair<true>(hp, items, 2 * pairs, smem, false, false, st);
             }
         }
+        if (delay16) return launch_pair<true, true>(hp, items, tune.n_ctas, smem, odd, pairs_from_table, st);
         return launch_pair<true>(hp, items, tune.n_ctas, smem, odd, pairs_from_table, st);
     }
     const int ctas = std::min(items, tune.n_ctas > 0 ? tune.n_ctas : sm_count());
@@ -2228,6 +2283,32 @@ int xe_correlate_packets(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stri
     xe_job j{nullptr, vis, s, accumulate ? 1 : 0, 0};
     const size_t used = (size_t)(base - static_cast<uint8_t *>(ws)) + owner_bytes;
     return corr::run_batched(&j, 1, nullptr, base + owner_bytes, ws_bytes - used, st, &src);
+}
+
+int xe_correlate_packets_shifted(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
+                                 int32_t gps, xe_shape s, const int32_t *delays, int32_t *vis, int accumulate,
+                                 uint8_t *filled, uint32_t *lost, uint32_t *stats, void *ws, size_t ws_bytes,
+                                 void *stream) {
+    const size_t need = xe_correlate_packets_workspace_size(s);
+    if (need == 0 || !delays) return XE_EINVAL;
+    // one delay per block of 16 inputs, within the frame
+    int32_t d16[XE_MAX_INPUTS / 16];
+    for (int b = 0; b < s.n_inputs / 16; ++b) {
+        d16[b] = delays[16 * b];
+        if (d16[b] < 0 || d16[b] > s.n_time) return XE_EINVAL;
+        for (int k = 1; k < 16; ++k)
+            if (delays[16 * b + k] != d16[b]) return XE_EINVAL;
+    }
+    if (!ws || ws_bytes < need) return XE_ENOMEM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(ws) + 1023) & ~uintptr_t(1023));
+    const size_t owner_bytes = (size_t)round_up((int64_t)(s.n_time / 4) * (s.n_chan / 8) * 4, 1024);
+    uint32_t *owner = reinterpret_cast<uint32_t *>(base);
+    if (int e = xe::index_streams(pkts, n_pkts, pkt_stride, seq0, gps, 0, s, filled, lost, stats, owner, st)) return e;
+    xe::packet_src src{n_pkts ? pkts : base, owner, pkt_stride};
+    xe_job j{nullptr, vis, s, accumulate ? 1 : 0, 0};
+    const size_t used = (size_t)(base - static_cast<uint8_t *>(ws)) + owner_bytes;
+    return corr::run_batched(&j, 1, nullptr, base + owner_bytes, ws_bytes - used, st, &src, d16);
 }
 
 }  // extern "C"

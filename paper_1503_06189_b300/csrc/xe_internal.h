@@ -71,7 +71,7 @@ int correlate_legacy(const xe_job *jobs, int n_jobs, bool s8, cudaStream_t st);
 }  // namespace legacy
 
 inline bool valid_shape(const xe_shape &s) {
-    return s.n_inputs >= 16 && s.n_inputs <= 4096 && s.n_inputs % 16 == 0 && s.n_chan >= 1 &&
+    return s.n_inputs >= 16 && s.n_inputs <= XE_MAX_INPUTS && s.n_inputs % 16 == 0 && s.n_chan >= 1 &&
            s.n_time >= 0;
 }
 

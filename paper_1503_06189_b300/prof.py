@@ -38,6 +38,9 @@ def main(argv=None):
                     help="packets: re-lay the packets at a 128-byte multiple stride with 128-byte aligned payloads")
     ap.add_argument("--zero-copy-only", action="store_true",
                     help="packets: time xe_correlate_packets only (no assembled frame is allocated)")
+    ap.add_argument("--shift-max", type=int, default=-1,
+                    help="packets: read the samples time-shifted (one delay per 16 inputs, 0 .. this many "
+                         "samples) with xe_correlate_packets_shifted; the two-step path then shifts the frame")
     ap.add_argument("--spread", type=int, default=64, help="shift: delays drawn from 0 .. spread samples")
     ap.add_argument("--uniform", action="store_true", help="shift: one delay per block of 16 inputs")
     a = ap.parse_args(argv)
@@ -104,12 +107,29 @@ def main(argv=None):
             wsa = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device=dev)
             wsc = torch.empty(xe.xe_correlate_workspace_size(s), dtype=torch.uint8, device=dev)
 
+        import numpy as np
+        delays = None
+        if a.shift_max >= 0:
+            rs = np.random.default_rng(5)
+            delays = np.repeat(rs.integers(0, min(a.shift_max, T) + 1, N // 16), 16).astype(np.int32)
+            if not a.zero_copy_only:
+                shifted = torch.empty_like(out)
+
         def zero_copy():
-            xe.xe_correlate_packets(pk, pk.shape[0], pk.shape[1], 0, 1, s, vis, a.accumulate, filled, lost, stats, ws)
+            if delays is None:
+                xe.xe_correlate_packets(pk, pk.shape[0], pk.shape[1], 0, 1, s, vis, a.accumulate, filled, lost, stats,
+                                        ws)
+            else:
+                xe.xe_correlate_packets_shifted(pk, pk.shape[0], pk.shape[1], 0, 1, s, delays, vis, a.accumulate,
+                                                filled, lost, stats, ws)
 
         def two_step():
             xe.xe_assemble(pk, pk.shape[0], pk.shape[1], 0, 1, s, out, filled, lost, stats, wsa)
-            xe.xe_correlate(out, s, vis, a.accumulate, wsc)
+            if delays is None:
+                xe.xe_correlate(out, s, vis, a.accumulate, wsc)
+            else:
+                xe.xe_time_shift(out, s, delays, shifted)
+                xe.xe_correlate(shifted, s, vis, a.accumulate, wsc)
 
         cmac = F * P * T
         runs = (("zero-copy", zero_copy),) + (() if a.zero_copy_only else (("two-step", two_step),))

@@ -159,3 +159,122 @@ def test_time_shift_in_the_frame_pipeline():
     ref = oracle.normalize(want, n)
     o = out.cpu().numpy()
     assert np.all(np.abs(o - ref) <= REL_TOL * np.abs(ref))
+
+
+def _block_delays(rng, N, T, hi):
+    """One delay per block of 16 inputs, in [0, min(hi, T)], expanded to one per input; the first
+    block unshifted and, where T allows, one block shifted by the whole frame."""
+    b = rng.integers(0, min(hi, T) + 1, N // 16)
+    b[0] = 0
+    if N >= 64:
+        b[-1] = T
+    return np.repeat(b, 16)
+
+
+def _shifted_packets(pk, N, F, T, gps, d, accumulate=False, vis=None):
+    s = xe.Shape(N, F, T)
+    vis = torch.zeros((F, xe.npairs(N), 2), dtype=torch.int32, device="cuda") if vis is None else vis
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device="cuda")
+    lost = torch.zeros(F, dtype=torch.int32, device="cuda")
+    stats = torch.zeros(5, dtype=torch.int32, device="cuda")
+    ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device="cuda")
+    xe.xe_correlate_packets_shifted(X.dev(pk), pk.shape[0], pk.shape[1], 0, gps, s, d, vis, accumulate, filled,
+                                    lost, stats, ws)
+    torch.cuda.synchronize()
+    return vis, filled, lost, stats
+
+
+@pytest.mark.parametrize("N,F,T,hi", [(256, 16, 4096, 300),    # fold items (one per channel)
+                                      (512, 8, 2048, 2048),    # fold items and Gram singles between super-blocks
+                                      (128, 16, 16384, 700),   # Gram blocks, twins (T >= 16384)
+                                      (64, 8, 1028, 1028),     # Gram blocks, wide singles; ragged time tail
+                                      (272, 8, 516, 64),       # a half super-block at the end (Gram single)
+                                      (16, 8, 4, 4)])          # one slot
+def test_shifted_packets_match_oracle(N, F, T, hi):
+    """xe_correlate_packets_shifted (delays applied while the packets are read) equals assembly,
+    time shift and correlation on the oracle, bit for bit, with lost, duplicated and reordered
+    packets; the index outputs equal xe_correlate_packets'."""
+    rng = np.random.default_rng(N * 7 + T)
+    gps = 1
+    fr = synth.uniform_frame(N, F, T, N + 5 * T)
+    pk = synth.packet_stream(fr, 0, gps, seed=N + T, p_drop=0.02, p_reorder=0.05, p_dup=0.02)
+    d = _block_delays(rng, N, T, hi)
+    vis, filled, lost, stats = _shifted_packets(pk, N, F, T, gps, d)
+    fo, filled_o, lost_o, _ = oracle.assemble(pk, 0, gps, N, F, T)
+    want, st = oracle.correlate(oracle.time_shift(fo, d))
+    assert st == oracle.OK
+    np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want)
+    np.testing.assert_array_equal(lost.cpu().numpy().astype(np.int64), lost_o.astype(np.int64))
+    np.testing.assert_array_equal(filled.cpu().numpy(), filled_o)
+
+
+def test_shifted_packets_equal_the_two_pass_path_and_accumulate():
+    """Full-band geometry, 8 frames per call, accumulating onto earlier visibilities: the fused path
+    equals xe_assemble -> xe_time_shift -> xe_correlate on the device, and on sampled channels the
+    oracle."""
+    rng = np.random.default_rng(21)
+    N, F, T, gps = 256, 64, 8192, 8
+    s = xe.Shape(N, F, T)
+    fr = synth.signal_frame(N, F, T, 22)
+    pk = synth.packet_stream(fr, 0, gps, seed=23, p_drop=0.001, p_reorder=0.005, p_dup=0.001)
+    d = _block_delays(rng, N, T, 4096)
+    start = torch.randint(-1000, 1000, (F, xe.npairs(N), 2), dtype=torch.int32, device="cuda")
+    vis, _, _, _ = _shifted_packets(pk, N, F, T, gps, d, accumulate=True, vis=start.clone())
+    frame = torch.empty((T, F, N), dtype=torch.uint8, device="cuda")
+    shifted = torch.empty_like(frame)
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device="cuda")
+    lost = torch.zeros(F, dtype=torch.int32, device="cuda")
+    stats = torch.zeros(5, dtype=torch.int32, device="cuda")
+    ws = torch.empty(xe.xe_assemble_workspace_size(s), dtype=torch.uint8, device="cuda")
+    xe.xe_assemble(X.dev(pk), pk.shape[0], pk.shape[1], 0, gps, s, frame, filled, lost, stats, ws)
+    xe.xe_time_shift(frame, s, d, shifted)
+    two = X.correlate(shifted, start.clone(), accumulate=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(vis.cpu().numpy(), two.cpu().numpy())
+    fo, _, _, _ = oracle.assemble(pk, 0, gps, N, F, T)
+    so = oracle.time_shift(fo, d)
+    for f in (0, 17, 63):
+        want, _ = oracle.correlate(np.ascontiguousarray(so[:, f:f + 1, :]))
+        np.testing.assert_array_equal(vis[f].cpu().numpy().astype(np.int64) - start[f].cpu().numpy(), want[0])
+
+
+def test_shifted_packets_zero_delays_equal_unshifted_and_reject_bad_delays():
+    """Zero delays give xe_correlate_packets' result; delays out of [0, T] or differing within a block
+    of 16 inputs are rejected before any work."""
+    N, F, T, gps = 256, 8, 1024, 1
+    s = xe.Shape(N, F, T)
+    fr = synth.uniform_frame(N, F, T, 31)
+    pk = synth.packet_stream(fr, 0, gps, seed=32, p_drop=0.01, p_reorder=0.02, p_dup=0.01)
+    vis0, _, _, _ = _shifted_packets(pk, N, F, T, gps, np.zeros(N, int))
+    ref = torch.zeros_like(vis0)
+    filled = torch.empty((T // 4, F // 8), dtype=torch.uint8, device="cuda")
+    lost = torch.zeros(F, dtype=torch.int32, device="cuda")
+    stats = torch.zeros(5, dtype=torch.int32, device="cuda")
+    ws = torch.empty(xe.xe_correlate_packets_workspace_size(s), dtype=torch.uint8, device="cuda")
+    xe.xe_correlate_packets(X.dev(pk), pk.shape[0], pk.shape[1], 0, gps, s, ref, False, filled, lost, stats, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(vis0, ref)
+    bad = [np.full(N, -1), np.full(N, T + 1), np.r_[np.zeros(N - 1, int), 1]]
+    for d in bad:
+        with pytest.raises(xe.XeError):
+            _shifted_packets(pk, N, F, T, gps, d)
+
+
+def test_shifted_packets_balanced_split():
+    """The shifted reads in a launch whose pieces start part-way into a channel (XE_LAYOUT_FOLD_SPLIT,
+    80 channels of 5 stages on at most 74 pairs): pieces begin kt0 stages in, at the delayed slots."""
+    rng = np.random.default_rng(41)
+    N, F, T, gps = 256, 80, 516, 1
+    fr = synth.uniform_frame(N, F, T, 42)
+    pk = synth.packet_stream(fr, 0, gps, seed=43, p_drop=0.02, p_reorder=0.05, p_dup=0.02)
+    d = _block_delays(rng, N, T, 400)
+    saved = xe.xe_tune_table_get()
+    xe.xe_tune_table_set([dict(n_inputs=N, t_bucket=1024, mode=xe.XE_TUNE_PACKETS, layout=xe.XE_LAYOUT_FOLD_SPLIT,
+                               pairs=0, odd_pairs=0, k_flush=0)])
+    try:
+        vis, _, _, _ = _shifted_packets(pk, N, F, T, gps, d)
+    finally:
+        xe.xe_tune_table_set(saved)
+    fo, _, _, _ = oracle.assemble(pk, 0, gps, N, F, T)
+    want, _ = oracle.correlate(oracle.time_shift(fo, d))
+    np.testing.assert_array_equal(vis.cpu().numpy().astype(np.int64), want)
