@@ -662,10 +662,11 @@ constexpr int kPairConvFwdWarp = 2;           // forwards converter completion, 
 constexpr int kPairEpiFwdWarp = 3;            // forwards epilogue completion to the even CTA
 constexpr int kPairEpiWarp0 = 4;
 constexpr int kPairConvWarp0 = kPairEpiWarp0 + kPairEpiWarps;
-// Converter shape per mode. A stage is kKt samples; 16 converter warps in both kernels. Frame mode
-// (the 256-sample kernel): 256-sample stages (half the per-stage bookkeeping of 128: 0.80 against
-// 0.81 ms per full-band frame), two rows per thread, three register buffers (two stages in flight).
-// Packet mode (the 128-sample kernel): one row per thread and two buffers, one stage in flight.
+// Converter shape per mode. A stage is kKt samples; 16 converter warps and two register buffers
+// (one stage of samples in flight) in both kernels. Frame mode (the 256-sample kernel): 256-sample
+// stages (half the per-stage bookkeeping of 128: 0.80 against 0.81 ms per full-band frame), two rows
+// per thread; two buffers against three: 7.21 against 7.97 ms for N = 2048, 64 channels, T = 16384,
+// 0.79 against 0.86 ms for N = 1024. Packet mode (the 128-sample kernel): one row per thread.
 // Measured on the 8-frame full-band call shape (296 channels) and the one-frame call: 16 warps with
 // two buffers 1.12 / 0.587 ms, with three 1.12 / 0.622, with four 1.67 / 0.90; 8 warps of two rows
 // with four buffers 1.27 / 0.70, with three 1.22 / 0.65. The sample gathers in flight occupy L1,
@@ -677,7 +678,7 @@ struct PairShape {
     static constexpr int kConvWarps = 16;
     static constexpr int kRows = kKt * 4 / (32 * kConvWarps);
     static constexpr int kRowStep = kKt / kRows;
-    static constexpr int kBufs = kPackets ? 2 : 3;
+    static constexpr int kBufs = 2;
     static constexpr int kThreads = 32 * (kPairConvWarp0 + kConvWarps);
     // registers per thread: at launch (the __launch_bounds__ limit), and after the split between
     // the role, epilogue and converter warpgroups, which hands out exactly the registers the
@@ -1668,32 +1669,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(PairShape<kPackets>:
             if (++os == (uint32_t)p.op_stages) { os = 0; oph ^= 1; }
             return true;
         };
-        static_assert(S::kBufs == 2 || S::kBufs == 3, "the rotations below use two or three buffers");
-        Buf x, y, z;
+        static_assert(S::kBufs == 2, "the rotation below uses two buffers");
+        Buf x, y;
 #pragma unroll
-        for (int q = 0; q < kOwn; ++q) x.own[q] = y.own[q] = z.own[q] = kNoPacket;
-        if constexpr (S::kBufs == 2) {
-            next_owners(x);                           // stages 0, 1
-            next_owners(y);
-            issue(x);
-            next_owners(x);                           // stage 2
-            for (;;) {
-                if (!step(y, x)) break;
-                if (!step(x, y)) break;
-            }
-        } else {
-            next_owners(x);                           // stages 0, 1, 2
-            next_owners(y);
-            next_owners(z);
-            issue(x);
-            next_owners(x);                           // stage 3
-            issue(y);
-            next_owners(y);                           // stage 4
-            for (;;) {
-                if (!step(z, x)) break;
-                if (!step(x, y)) break;
-                if (!step(y, z)) break;
-            }
+        for (int q = 0; q < kOwn; ++q) x.own[q] = y.own[q] = kNoPacket;
+        next_owners(x);                               // stages 0, 1
+        next_owners(y);
+        issue(x);
+        next_owners(x);                               // stage 2
+        for (;;) {
+            if (!step(y, x)) break;
+            if (!step(x, y)) break;
         }
     }
 
