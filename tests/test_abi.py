@@ -57,3 +57,24 @@ def test_binding_rejects_host_and_strided_buffers():
     with pytest.raises(ValueError, match="contiguous"):
         xe._ptr(torch.zeros((4, 8), dtype=torch.uint8).t())
     assert xe._ptr(1 << 20) == 1 << 20 and xe._dptr(None) is None
+
+
+def test_shifted_packet_call_checks_delays_on_the_host():
+    """xe_correlate_packets_shifted validates its host delays before it touches a device buffer:
+    a delay out of [0, T] or one that differs within a block of 16 inputs is XE_EINVAL, and valid
+    delays then fail only on the missing workspace (XE_ENOMEM)."""
+    import numpy as np
+
+    lib = xe.lib()
+    N, F, T = 64, 8, 1024
+    s = xe.Shape(N, F, T)
+
+    def call(d):
+        d = np.ascontiguousarray(np.asarray(d, dtype=np.int32))
+        return lib.xe_correlate_packets_shifted(None, 0, 16 + 32 * N, 0, 1, s, d.ctypes.data, None, 0, None, None,
+                                                None, None, 0, None)
+
+    assert call(np.full(N, -1)) == xe.XE_EINVAL
+    assert call(np.full(N, T + 1)) == xe.XE_EINVAL
+    assert call(np.r_[np.zeros(N - 1, int), 1]) == xe.XE_EINVAL          # differs inside the last block
+    assert call(np.repeat([0, T, 7, 300], 16)) == xe.XE_ENOMEM
