@@ -682,9 +682,9 @@ struct PairShape {
     static constexpr int kThreads = 32 * (kPairConvWarp0 + kConvWarps);
     // registers per thread: at launch (the __launch_bounds__ limit), and after the split between
     // the role, epilogue and converter warpgroups, which hands out exactly the registers the
-    // launch allocates. The 128-sample kernel: roles 48, fold epilogue 112, converters 80; the
-    // 256-sample kernel: roles 32, Gram epilogue 96, converters (two rows, three buffers) 88. Both
-    // splits are the ones without spills (the compiler reports 20 and 0 bytes of spill stores)
+    // launch allocates. The 128-sample kernel: roles 48, fold epilogue 112, converters 80 (the
+    // split with the fewest spills: 20 bytes of spill stores); the 256-sample kernel: roles 32, Gram
+    // epilogue 96, converters (two rows) 88, without spills
     static constexpr int kRegsLaunch = 65536 / kThreads / 8 * 8;
     static constexpr int kRegsRoles = kPackets ? 48 : 32;
     static constexpr int kRegsEpi = kPackets ? 112 : 96;
