@@ -112,8 +112,8 @@ int xe_assemble(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint6
  * device current); so does the first call after the device's context has been reset, since the
  * array then lives at a new address. Make that first call before any stream capture; a call with
  * n_pkts = 0 on a small shape serves. The call allocates nothing. All calls share the one array
- * and each call resets the part it uses, so calls whose kernels may overlap on the GPU (different
- * streams, or overlapping graph nodes) race and must be serialised by the caller.
+ * and each call resets the part it uses, so calls whose kernels may overlap on the GPU (for
+ * example on different streams) race and must be serialised by the caller.
  */
 #define XE_ASSEMBLE_NOALLOC_MAX_SLOTS (1 << 18)
 int xe_assemble_noalloc(const uint8_t *pkts, uint32_t n_pkts, uint32_t pkt_stride, uint64_t seq0,
